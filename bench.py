@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Throughput of the batched Parallel-Tempering path (smoothed-cubic 4-body random-laser model).
+
+Workload (one GPU): N = 256 modes, 16 disorder samples x 48 temperatures (geometric 0.25-1.6) x 2
+replicas = 1536 chains, FP32 amplitudes/fields with FP64 energies.  One step = one swap interval:
+64 sweeps of every chain, the FP64-accumulated resync, 4 measurements (E, Y2, Y4, q histogram) and a
+swap pass.  Metric: chain-sweeps/s.  Inputs are synthetic (Gaussian couplings, sigma_J = 1/N, on the
+comb graph); the coupling store (16 x 22 MB) is larger than L2, so no flush is needed between steps.
+
+Also reported: the plain FP64 GPU sweep (the paper's design) on the same workload, the roofline of
+the sweep kernel, an end-to-end number through host buffers, and the FP64 CPU oracle on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEP_SWEEPS = 64
+N_MODES = 256
+CPU_SAMPLE_SECONDS = 15.0
+
+
+# ------------------------------------------------------------------------------------------- accounting
+def flops_per_chain_sweep(N: int) -> float:
+    """Algorithmic FP32 flops of one sweep (N/2 pair updates) of the pair-factored field evaluation,
+    averaged exactly over the pair distribution (j uniform, k uniform among the other modes):
+    per pair product z = a_x a_y (6 flops) used by either field, per coupling term acc += J z (4),
+    per field row h += conj(a_m) acc (8)."""
+    s = np.arange(2 * N - 1)
+    m = np.array([max(0, (ss - 1) // 2 - max(0, ss - (N - 1)) + 1) if ss >= 1 else 0 for ss in s])
+    K = np.arange(N)
+    tot = 0.0
+    for j in range(N):
+        inj = (s - j >= 0) & (s - j < N) & (s != 2 * j)
+        kk = K[K != j]
+        ink = (s[None, :] - kk[:, None] >= 0) & (s[None, :] - kk[:, None] < N) & (s[None, :] != 2 * kk[:, None])
+        tj = np.where(inj, m - 1, 0)[None, :]
+        tk = np.where(ink, m[None, :] - 1, 0)
+        both = inj[None, :] & ink
+        union = np.where(both, np.where(s[None, :] == j + kk[:, None], m - 1, m), np.where(inj[None, :] | ink, m - 1, 0))
+        rows = (tj > 0).sum() * len(kk) + (tk > 0).sum()
+        tot += 6.0 * union.sum() + 4.0 * (tj.sum() * len(kk) + tk.sum()) + 8.0 * rows
+    return tot / (N * (N - 1)) * (N / 2)
+
+
+def peak_fp32_tflops(sm_count=152, mhz=2070.0):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.rows, self.proc, self.idx = [], None, gpu_index
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows if len(r) >= 8 for n, v in zip(names, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------- CPU oracle
+def _oracle_worker(args):
+    N, nq, seed, sweeps, temps = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2511_13508_gb300 import workload
+    J = workload.couplings(N, nq, seed)
+    pt = oracle.OraclePT([N], [J], temps, 1, 17, swap_every=0, measure_every=16, resync_every=64)
+    t0 = time.perf_counter()
+    pt.sweep(sweeps)
+    return sweeps * len(temps), time.perf_counter() - t0
+
+
+def cpu_oracle_rate(target_seconds=CPU_SAMPLE_SECONDS, workers=None):
+    """Oracle chain-sweeps/s on the host cores: independent processes (spawned), each running a few
+    N=256 chains of the same workload for a bounded number of sweeps."""
+    workers = workers or os.cpu_count() or 1
+    import oracle
+    nq = len(oracle.enumerate_quads(N_MODES))
+    # calibrate: one chain, one sweep
+    t_one = _oracle_worker((N_MODES, nq, 301, 1, [0.25]))[1]
+    per_worker = max(1, int(target_seconds / max(t_one, 1e-3)))
+    temps = [0.25, 1.6]
+    sweeps = max(1, per_worker // len(temps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(N_MODES, nq, 301 + i, sweeps, temps) for i in range(workers)])
+        wall = time.perf_counter() - t0
+    done = sum(r[0] for r in res)
+    return {"value": done / wall, "unit": "chain-sweeps/s", "cores": workers, "kind": "oracle",
+            "sample": "%d processes x %d chains (N=256, T=0.25 and 1.6) x %d sweeps, FP64, single-threaded each"
+                      % (workers, len(temps), sweeps)}
+
+
+# ------------------------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, dist):
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+
+    torch.cuda.set_device(rank % torch.cuda.device_count())
+    pkg.build()
+    W = workload.workloads()["n256_large"]
+    nq = len(pkg.enumerate_quads(N_MODES))
+    seeds = [s + 1000 * rank for s in W.seeds]  # weak scaling: every rank its own 16 samples
+    Js = [workload.couplings(N_MODES, nq, s) for s in seeds]
+    stream = torch.cuda.Stream()
+    kw = dict(swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
+    pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 12345 + rank, precision="fp32", stream=stream, **kw)
+    chains = pt.n_chains
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pt.sweep(STEP_SWEEPS)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pt.sweep(STEP_SWEEPS)
+        ev1.record(stream)
+        barrier()
+    pt.sync()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cs = chains * STEP_SWEEPS * args.steps * world
+    value = total_cs / (ms / 1e3)
+
+    # ---- sweep kernel alone (roofline): one launch of 64 sweeps without measurement/resync/swap
+    pk = pkg.PT(W.Ns, Js, W.temps, W.replicas, 777, precision="fp32", stream=stream, swap_every=0,
+                measure_every=0, resync_every=0, use_graphs=False)
+    pk.sweep(STEP_SWEEPS)
+    pk.sync()
+    reps = 3
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        pk.sweep(STEP_SWEEPS)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    kms = ev0.elapsed_time(ev1) / reps
+    fl = flops_per_chain_sweep(N_MODES) * chains * STEP_SWEEPS
+    clocks = clk.summary()
+    peak = peak_fp32_tflops()
+    achieved = fl / (kms / 1e3) / 1e12
+    pk.close()
+
+    # ---- plain FP64 GPU sweep (paper's design) on the same workload, bounded sample
+    pp = pkg.PT(W.Ns, Js, W.temps, W.replicas, 4242, precision="fp64_plain", stream=stream, **kw)
+    pp.sweep(1)
+    pp.sync()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    pp.sweep(2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_rate = chains * 2 / (ev0.elapsed_time(ev1) / 1e3)
+    pp.close()
+
+    # ---- end to end through host buffers: state in (h2d), one step, observables + state out (d2h)
+    a_host, _ = pt.state()
+    a_host = np.ascontiguousarray(a_host)
+    pt.sync()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(e2e_steps):
+        pt.set_state(a_host)
+        pt.sweep(STEP_SWEEPS)
+        obs = pt.observables()
+        a_host, _ = pt.state()
+    wall = time.perf_counter() - t0
+    h2d = a_host.size * 8  # FP32 complex amplitudes uploaded
+    d2h = sum(v.nbytes for v in obs.values()) + a_host.size * 8 + chains * 8
+    e2e = {"value": chains * STEP_SWEEPS * e2e_steps * world / wall, "unit": "chain-sweeps/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    pt.close()
+    return dict(value=value, ms=ms, kms=kms, achieved=achieved, peak=peak, clocks=clocks, plain_rate=plain_rate,
+                e2e=e2e, fl=fl)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
+           "samples_per_gpu": 16, "temps": 48, "replicas": 2, "N": N_MODES, "step": "64 sweeps + resync + "
+           "4 measurements + swap pass", "l2": "inputs larger than L2 (352 MB coupling store)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        # the reference arm is the FP64 CPU oracle, bounded per step
+        per = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+        for _ in range(args.warmup):
+            cpu_oracle_rate(target_seconds=per / 4)
+        vals = [cpu_oracle_rate(target_seconds=per) for _ in range(args.steps)]
+        v = statistics.mean(x["value"] for x in vals)
+        line = {"metric": "chain-sweeps/s at N=256", "value": v, "unit": "chain-sweeps/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                "impl": "reference",
+                "cpu_baseline": {"value": v, "unit": "chain-sweeps/s", "cores": vals[0]["cores"], "kind": "oracle",
+                                 "sample": vals[0]["sample"]},
+                "e2e": {"value": v, "unit": "chain-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    # CPU baseline first (spawned processes, before the first GPU call)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    r = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        line = {"metric": "chain-sweeps/s at N=256", "value": r["value"], "unit": "chain-sweeps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
+                             "frac": r["achieved"] / r["peak"], "traffic": None,
+                             "kernel": "sweep_kernel<float,8,16>", "kernel_ms_per_launch": r["kms"],
+                             "flops_per_launch": r["fl"],
+                             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)"},
+                "cpu_baseline": cpu,
+                "e2e": r["e2e"],
+                "clocks": r["clocks"],
+                "gpu_launches": 5 * args.steps,
+                "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
+                                   "speedup_fp32": r["value"] / world / r["plain_rate"]}}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

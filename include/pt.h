@@ -1,0 +1,181 @@
+/*
+ * pt.h -- C ABI of the GB300 (sm_103a) Parallel-Tempering engine for the smoothed-cubic
+ * 4-body random-laser model of arXiv 2511.13508.
+ *
+ * The model (paper Sec. II): N complex mode amplitudes a_k on the complete mode-locked comb
+ * graph (omega_k = k), quadruplets a<b<c<d with a+d = b+c (frequency matching condition,
+ * Eq. (1)), real Gaussian couplings J_q, Hamiltonian Eq. (4)
+ *     H = -cc * sum_q J_q Re( conj(a_a) a_b a_c conj(a_d) ),   cc = 2 ("+ c.c."),
+ * sampled from P[a] ~ exp(-beta H) delta(N - sum_k |a_k|^4) (Eq. (8)) with the
+ * constraint-preserving pair Metropolis move (Sec. III.A.1) and exchange Monte Carlo between
+ * neighbouring temperatures (Sec. III.A.2, Eq. (15)).  Observables: energy moments for the
+ * specific heat (Eq. (21)), the replica overlap q and its 201-bin histogram (Sec. IV.C), the
+ * inverse participation ratios Y2, Y4 (Sec. IV.D).
+ *
+ * Conventions shared by every call:
+ *  - S disorder samples, sample s has N[s] modes (even, 4 <= N <= 512), R replicas and n_T
+ *    temperatures (ascending, index 0 = coldest).  A "chain" is one (sample, replica,
+ *    temperature) configuration; canonical chain order is (s, r, t), t fastest.
+ *  - Complex arrays are interleaved (re, im) doubles; a state array holds, in canonical chain
+ *    order, N[s] complex amplitudes per chain (total sum_s N[s]*R*n_T complex numbers).
+ *  - Every call returns an int status: PT_OK (0) or a negative PT_E* code.  No call aborts or
+ *    throws.  pt_last_error() gives a static, human-readable message for the last failure.
+ *  - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *    counters (stream, sweep, update, tag); the streams are documented in the design notes and
+ *    make a run reproducible bit-for-bit for a given precision, seed and kernel configuration.
+ *  - Device work runs asynchronously on the stream given to pt_create; calls that return host
+ *    data (pt_measure, pt_get_state, pt_fields, pt_energy, pt_save) synchronise that stream.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define PT_OK 0
+#define PT_EINVAL (-1)       /* bad argument: N odd or out of range, temps not ascending/positive, ... */
+#define PT_ENOMEM (-2)       /* device or host allocation failed */
+#define PT_ECUDA (-3)        /* a CUDA runtime call failed (message in pt_last_error) */
+#define PT_ETIMEOUT (-4)     /* a bounded device wait or the host watchdog ran out */
+#define PT_ENAN (-5)         /* non-finite coupling, or non-finite state found at resync */
+#define PT_ESTATE (-6)       /* checkpoint bytes do not match this context */
+#define PT_EUNSUPPORTED (-7) /* valid request this build does not implement */
+
+/* ---------------------------------------------------------------- precision */
+#define PT_PREC_FP32 0       /* FP32 fields/moves, FP64 running energy, resync, swap log-ratio */
+#define PT_PREC_FP64 1       /* the same J-sharing kernels in FP64 throughout */
+#define PT_PREC_FP64_PLAIN 2 /* the paper's GPU design restated: one thread per quadruplet term of
+                                Delta E, tree reduction, one chain per thread block, no J sharing, FP64 */
+
+#define PT_QBINS 201 /* overlap histogram: bins centred at -1, -0.99, ..., 1 */
+#define PT_NSTAT 7   /* per (sample, T): n, sumE, sumE^2, sumY2, sumY4, sumI, sumI^2  (I = sum |a|^2) */
+#define PT_NQSTAT 5  /* per (sample, T): n, sum q, sum q^2, sum q^3, sum q^4 over replica pairs */
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc returns NULL on failure. */
+typedef void *(*pt_alloc_fn)(size_t bytes, void *user);
+typedef void (*pt_free_fn)(void *ptr, void *user);
+
+typedef struct pt_config {
+    int precision;        /* PT_PREC_*; default PT_PREC_FP32 */
+    double cc_factor;     /* multiplier of the quadruplet sum in H; default 2 ("+ c.c." of Eq. (4)) */
+    int swap_every;       /* sweeps between swap passes (paper: 64); 0 = only on pt_swap() */
+    int measure_every;    /* sweeps between measurements; 0 = never */
+    int resync_every;     /* sweeps between renormalisation + full FP64-accumulated H; 0 = never */
+    int chains_per_block; /* chains sharing one J stream inside a thread block: 0 = tuned, or 8/16/32 */
+    int sweeps_per_unit;  /* sweeps in one scheduling unit of the persistent kernel; 0 = tuned */
+    int blocks_per_sm;    /* persistent thread blocks per SM; 0 = tuned */
+    int use_graphs;       /* replay each sweep segment as a captured CUDA graph (default 1) */
+    int watchdog_ms;      /* host watchdog on synchronising calls; 0 = wait forever (default 600000) */
+} pt_config;
+
+/* Fills *cfg with the defaults above.  Cannot fail. */
+void pt_config_default(pt_config *cfg);
+
+typedef struct pt_ctx pt_ctx; /* opaque; owned by the library */
+
+/* Observable accumulators, copied out by pt_measure into caller-owned buffers (any may be NULL).
+ * Layouts (C order):  stat [S][n_T][PT_NSTAT]   qstat [S][n_T][PT_NQSTAT]   qhist [S][n_T][PT_QBINS]
+ *                     swap_acc, swap_att [S][R][n_T-1]    mc_acc, mc_att [S][n_T]
+ * stat and qstat count one entry per chain (stat) or replica pair (qstat) per measurement. */
+typedef struct pt_observables {
+    double *stat;
+    double *qstat;
+    uint64_t *qhist;
+    uint64_t *swap_acc;
+    uint64_t *swap_att;
+    uint64_t *mc_acc;
+    uint64_t *mc_att;
+} pt_observables;
+
+/* Canonical quadruplet list of the N-mode comb (paper Sec. II.C "Graph generation"; Eq. (1) with
+ * omega_k = k): every a<b<c<d with a+d = b+c, lexicographic in (a,b,c).  Writes 4*count int32 to
+ * abcd when abcd != NULL; *count receives the count.  This is the order of J in pt_create.
+ * PT_EINVAL if N < 4 or N > 512 or count == NULL. */
+int pt_enumerate_quads(int N, int32_t *abcd, int64_t *count);
+
+/* Creates a context and uploads everything; the host->device boundary is crossed here.
+ *  cfg        NULL = defaults.
+ *  S, N[S]    samples and their mode counts (each even, 4..512).
+ *  J          couplings of all samples back to back, each in canonical quadruplet order;
+ *  J_offsets  [S+1] start of each sample in J (J_offsets[s+1]-J_offsets[s] must equal the count).
+ *  n_T, temps temperatures (positive, strictly ascending).
+ *  replicas   R >= 1 (overlaps need R >= 2).
+ *  seed       Philox key.  Initial chains are exact draws of the beta = 0 law (uniform on the
+ *             constraint surface), then E = H(a) is computed on the device.
+ *  alloc/free optional device allocator (both or neither); alloc_user is passed through.
+ *  stream     cudaStream_t to run on; NULL = a non-blocking stream owned by the context (the legacy
+ *             default stream cannot be captured into CUDA graphs).
+ * Caller keeps ownership of every input array; they are copied.  On failure *out is NULL. */
+int pt_create(pt_ctx **out, const pt_config *cfg, int S, const int32_t *N, const double *J,
+              const int64_t *J_offsets, int n_T, const double *temps, int replicas, uint64_t seed,
+              pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);
+
+/* Runs n_sweeps Monte Carlo sweeps (one sweep = N/2 pair updates per chain, Sec. III.A.1) on every
+ * chain, asynchronously.  After each completed sweep t (counted from creation) the schedule is:
+ * resync if t % resync_every == 0, measure if t % measure_every == 0, swap pass if
+ * t % swap_every == 0.  All chains of one sample update the same (j,k) pair sequence. */
+int pt_sweep(pt_ctx *ctx, int64_t n_sweeps);
+
+/* One sequential swap pass over every (sample, replica) temperature ladder, ascending in T
+ * (Sec. III.A.2, Eq. (15)); exchanges temperature labels, asynchronously. */
+int pt_swap(pt_ctx *ctx);
+
+/* Renormalises every chain onto sum|a|^4 = N and recomputes E = H(a) in full (asynchronous). */
+int pt_resync(pt_ctx *ctx);
+
+/* Measures every chain now (same accumulators as the schedule), asynchronously. */
+int pt_measure_now(pt_ctx *ctx);
+
+/* Copies the accumulated observables into *out (synchronous). */
+int pt_measure(pt_ctx *ctx, pt_observables *out);
+
+/* Zeroes all accumulators (e.g. after burn-in; paper Sec. III.B uses the last half of the run). */
+int pt_reset_observables(pt_ctx *ctx);
+
+/* State in canonical chain order: a (interleaved complex doubles) and/or E (doubles); NULL skips. */
+int pt_get_state(pt_ctx *ctx, double *a, double *E);
+
+/* Replaces every chain's amplitudes (canonical order, as pt_get_state) and recomputes E on the
+ * device.  The state is taken as given (not renormalised). */
+int pt_set_state(pt_ctx *ctx, const double *a);
+
+/* Full recompute of H for every chain of the current state, canonical order, without changing it. */
+int pt_energy(pt_ctx *ctx, double *E);
+
+/* Per-step local fields (the sweep kernel's field phase, Sec. III.A.3): for the pair (j,k) and every
+ * chain of sample s, writes 8 doubles per chain in canonical (r, t) order:
+ *   h_j, h_k   (complex) local fields, H = -cc Re(conj(a_l) h_l) + terms without a_l;
+ *   B_jk       (complex) sum over quadruplets {j,m,k,y}, j+m = k+y, of J conj(a_m) a_y;
+ *   A_jk       (complex) sum over quadruplets {j,k,x,y}, x+y = j+k, of J a_x a_y;
+ * so that Delta H = -cc Re[ conj(dj) h_j + conj(dk) h_k + conj(dj) dk B_jk + conj(dj) conj(dk) A_jk ]
+ * for a_j += dj, a_k += dk.  Not available for PT_PREC_FP64_PLAIN (PT_EUNSUPPORTED). */
+int pt_fields(pt_ctx *ctx, int sample, int j, int k, double *out);
+
+/* Checkpoint.  pt_save with buf == NULL stores the needed size in *len; otherwise writes *len bytes
+ * (PT_EINVAL if *len is too small).  pt_load restores a checkpoint of a context created with the
+ * same arguments (PT_ESTATE otherwise); resuming is bit-identical to an uninterrupted run. */
+int pt_save(pt_ctx *ctx, void *buf, size_t *len);
+int pt_load(pt_ctx *ctx, const void *buf, size_t len);
+
+/* Counters: sweeps done since creation, swap passes done. */
+int pt_counters(pt_ctx *ctx, int64_t *sweeps_done, int64_t *swap_passes);
+
+/* Waits for the context's stream under the watchdog; reports device-side errors. */
+int pt_sync(pt_ctx *ctx);
+
+/* Frees everything; NULL-safe. */
+int pt_destroy(pt_ctx *ctx);
+
+/* Message of the last failing call on ctx (or of the last failing pt_create when ctx is NULL). */
+const char *pt_last_error(const pt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

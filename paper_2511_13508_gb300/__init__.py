@@ -1,0 +1,244 @@
+"""GB300 (sm_103a) Parallel-Tempering engine for the smoothed-cubic 4-body random-laser model
+(arXiv 2511.13508).
+
+Thin ctypes binding over the C ABI of ``libptgb.so`` (declared in ``include/pt.h``): argument
+marshalling only; every step of the Monte Carlo path runs in the library's CUDA kernels.  PyTorch
+supplies device memory (its caching allocator, through the ABI's allocator callbacks) and the
+stream.  There is no CPU fallback: without the compiled library the import of the engine fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["build", "lib", "PT", "enumerate_quads", "PREC", "PTError", "NSTAT", "NQSTAT", "QBINS"]
+
+PREC = {"fp32": 0, "fp64": 1, "fp64_plain": 2}
+NSTAT, NQSTAT, QBINS = 7, 5, 201
+_ERRORS = {-1: "PT_EINVAL", -2: "PT_ENOMEM", -3: "PT_ECUDA", -4: "PT_ETIMEOUT", -5: "PT_ENAN",
+           -6: "PT_ESTATE", -7: "PT_EUNSUPPORTED"}
+
+
+class PTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRORS.get(code, "PT_E?"), code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cc_factor", ctypes.c_double), ("swap_every", ctypes.c_int),
+                ("measure_every", ctypes.c_int), ("resync_every", ctypes.c_int),
+                ("chains_per_block", ctypes.c_int), ("sweeps_per_unit", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("use_graphs", ctypes.c_int), ("watchdog_ms", ctypes.c_int)]
+
+
+class Observables(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc", "mc_att")]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "pt_swap", "pt_resync",
+           "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
+           "pt_fields", "pt_save", "pt_load", "pt_counters", "pt_sync", "pt_destroy", "pt_last_error"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles libptgb.so for sm_103a (in-tree) if missing or stale."""
+    return _build.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libptgb.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError("libptgb.so is not built: run paper_2511_13508_gb300.build() (needs nvcc)")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i, i64, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.pt_config_default.argtypes = [ctypes.POINTER(Config)]; L.pt_config_default.restype = None
+        L.pt_enumerate_quads.argtypes = [i, vp, ctypes.POINTER(i64)]
+        L.pt_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), i, vp, vp, vp, i, vp, i, u64,
+                                ALLOC_FN, FREE_FN, vp, vp]
+        L.pt_sweep.argtypes = [vp, i64]
+        for n in ("pt_swap", "pt_resync", "pt_measure_now", "pt_reset_observables", "pt_sync", "pt_destroy"):
+            getattr(L, n).argtypes = [vp]
+        L.pt_measure.argtypes = [vp, ctypes.POINTER(Observables)]
+        L.pt_get_state.argtypes = [vp, vp, vp]
+        L.pt_set_state.argtypes = [vp, vp]
+        L.pt_energy.argtypes = [vp, vp]
+        L.pt_fields.argtypes = [vp, i, i, i, vp]
+        L.pt_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.pt_load.argtypes = [vp, vp, ctypes.c_size_t]
+        L.pt_counters.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.pt_last_error.argtypes = [vp]; L.pt_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _p(x: np.ndarray):
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def enumerate_quads(N: int) -> np.ndarray:
+    """Canonical quadruplets (a<b<c<d, a+d=b+c) of the N-mode comb, shape [|Q|, 4]."""
+    n = ctypes.c_int64()
+    _check(None, lib().pt_enumerate_quads(int(N), None, ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    _check(None, lib().pt_enumerate_quads(int(N), _p(out), ctypes.byref(n)))
+    return out[: n.value]
+
+
+def _check(h, rc):
+    if rc != 0:
+        raise PTError(rc, (lib().pt_last_error(h) or b"").decode())
+
+
+class _TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, stream):
+        import torch
+        self.torch, self.stream, self.dev = torch, stream, torch.cuda.current_device()
+
+        def _alloc(nbytes, user):
+            try:
+                return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.dev, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc, self.free = ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class PT:
+    """One Parallel-Tempering ensemble: S disorder samples x R replicas x n_T temperatures."""
+
+    def __init__(self, Ns, J_list, temps, replicas, seed, precision="fp32", cc=2.0, swap_every=64,
+                 measure_every=16, resync_every=64, chains_per_block=0, sweeps_per_unit=0, blocks_per_sm=0,
+                 use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True):
+        L = lib()
+        self.Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+        self.S, self.R = len(self.Ns), int(replicas)
+        self.temps = np.ascontiguousarray(temps, dtype=np.float64)
+        self.nT = len(self.temps)
+        self.precision = precision
+        J = np.ascontiguousarray(np.concatenate([np.asarray(j, np.float64) for j in J_list]))
+        off = np.zeros(self.S + 1, np.int64)
+        off[1:] = np.cumsum([len(j) for j in J_list])
+        cfg = Config()
+        L.pt_config_default(ctypes.byref(cfg))
+        cfg.precision = PREC[precision]; cfg.cc_factor = cc; cfg.swap_every = swap_every
+        cfg.measure_every = measure_every; cfg.resync_every = resync_every
+        cfg.chains_per_block = chains_per_block; cfg.sweeps_per_unit = sweeps_per_unit
+        cfg.blocks_per_sm = blocks_per_sm; cfg.use_graphs = int(bool(use_graphs)); cfg.watchdog_ms = watchdog_ms
+        self._alloc = None
+        s_ptr = None
+        if stream is not None:
+            s_ptr = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+        if torch_memory:
+            import torch
+            if torch.cuda.is_available():
+                if s_ptr is None or s_ptr == 0:
+                    # a stream of our own (the legacy default stream cannot be captured into graphs)
+                    self._stream = torch.cuda.Stream()
+                    s_ptr = int(self._stream.cuda_stream)
+                self._alloc = _TorchAllocator(s_ptr)
+        h = ctypes.c_void_p()
+        af = self._alloc.alloc if self._alloc else ALLOC_FN()
+        ff = self._alloc.free if self._alloc else FREE_FN()
+        rc = L.pt_create(ctypes.byref(h), ctypes.byref(cfg), self.S, _p(self.Ns), _p(J), _p(off), self.nT,
+                         _p(self.temps), self.R, ctypes.c_uint64(int(seed)), af, ff, None, s_ptr)
+        _check(None, rc)
+        self._h = h
+        self.n_chains = self.S * self.R * self.nT
+
+    # -------------------------------------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().pt_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def _c(self, rc):
+        _check(self._h, rc)
+
+    def sweep(self, n):
+        self._c(lib().pt_sweep(self._h, int(n)))
+
+    def swap(self):
+        self._c(lib().pt_swap(self._h))
+
+    def resync(self):
+        self._c(lib().pt_resync(self._h))
+
+    def measure_now(self):
+        self._c(lib().pt_measure_now(self._h))
+
+    def sync(self):
+        self._c(lib().pt_sync(self._h))
+
+    def reset_observables(self):
+        self._c(lib().pt_reset_observables(self._h))
+
+    def observables(self) -> dict:
+        S, R, nT = self.S, self.R, self.nT
+        np1 = max(nT - 1, 1)
+        o = dict(stat=np.zeros((S, nT, NSTAT)), qstat=np.zeros((S, nT, NQSTAT)),
+                 qhist=np.zeros((S, nT, QBINS), np.uint64), swap_acc=np.zeros((S, R, np1), np.uint64),
+                 swap_att=np.zeros((S, R, np1), np.uint64), mc_acc=np.zeros((S, nT), np.uint64),
+                 mc_att=np.zeros((S, nT), np.uint64))
+        ob = Observables(*[o[k].ctypes.data for k in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc", "mc_att")])
+        self._c(lib().pt_measure(self._h, ctypes.byref(ob)))
+        return o
+
+    def state(self):
+        """(amplitudes: complex128 [sum_s N_s R nT] in canonical (s, r, t) order, energies [S R nT])."""
+        tot = int(self.Ns.astype(np.int64).sum()) * self.R * self.nT
+        a = np.zeros(tot, np.complex128)
+        E = np.zeros(self.n_chains)
+        self._c(lib().pt_get_state(self._h, _p(a), _p(E)))
+        return a, E
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, np.complex128)
+        self._c(lib().pt_set_state(self._h, _p(a)))
+
+    def energy(self):
+        E = np.zeros(self.n_chains)
+        self._c(lib().pt_energy(self._h, _p(E)))
+        return E
+
+    def fields(self, sample, j, k):
+        """[R*nT, 4] complex: h_j, h_k, B_jk, A_jk for every chain of the sample, canonical (r, t) order."""
+        out = np.zeros(self.R * self.nT * 8)
+        self._c(lib().pt_fields(self._h, int(sample), int(j), int(k), _p(out)))
+        return out.view(np.complex128).reshape(self.R * self.nT, 4)
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t()
+        self._c(lib().pt_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._c(lib().pt_save(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._c(lib().pt_load(self._h, buf, len(blob)))
+
+    @property
+    def counters(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._c(lib().pt_counters(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value

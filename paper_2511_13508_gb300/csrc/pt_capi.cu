@@ -1,0 +1,974 @@
+// pt_capi.cu -- host orchestration and C ABI of the smoothed-cubic Parallel-Tempering engine
+// (arXiv 2511.13508): argument checks, the blocked per-mode coupling packer, device memory, the
+// sweep-segment scheduler (sweeps -> resync -> measure -> swap, replayed as CUDA graphs),
+// checkpoints and the host watchdog.  The declarations and their contracts are in include/pt.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pt.h"
+#include "pt_common.cuh"
+#include "pt_kernels.h"
+
+using namespace ptgb;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Counts the quadruplets of the N-mode comb: for every (a,b) with a<b the admissible c run over
+// b+1 .. N-1-(b-a) (then d = b+c-a lies in (c, N)).
+std::vector<int64_t> pair_offsets(int N, int64_t *total) {
+    std::vector<int64_t> off((size_t)N * N, -1);
+    int64_t n = 0;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) {
+            off[(size_t)a * N + b] = n;
+            const int cnt = N - 1 - 2 * b + a;
+            if (cnt > 0) n += cnt;
+        }
+    *total = n;
+    return off;
+}
+
+inline int xlo_of(int s, int N) { return std::max(0, s - (N - 1)); }
+inline int xhi_of(int s) { return (s - 1) / 2; }
+
+struct SampleLayout {
+    int N, ST, nblk;
+    std::vector<int> bo, xtlo, mode_blk, ebo;
+    std::vector<uint32_t> blkinfo;
+    int64_t jblocks;  // blocks of J stored for the sample
+};
+
+SampleLayout make_layout(int N) {
+    SampleLayout L;
+    L.N = N;
+    L.ST = (2 * N - 2 + TS - 1) / TS;
+    L.bo.assign(L.ST + 1, 0);
+    L.xtlo.assign(L.ST, 0);
+    for (int st = 0; st < L.ST; ++st) {
+        int xl = 1 << 30, xh = -1;
+        for (int s = st * TS; s < st * TS + TS; ++s) {
+            if (s < 1 || s > 2 * N - 3) continue;
+            const int lo = xlo_of(s, N), hi = xhi_of(s);
+            if (lo > hi) continue;
+            xl = std::min(xl, lo);
+            xh = std::max(xh, hi);
+        }
+        L.bo[st + 1] = L.bo[st];
+        if (xh >= 0) {
+            L.xtlo[st] = xl / TX;
+            for (int xt = xl / TX; xt <= xh / TX; ++xt) {
+                L.blkinfo.push_back(((uint32_t)st << 16) | (uint32_t)xt);
+                L.bo[st + 1]++;
+            }
+        }
+    }
+    L.nblk = L.bo[L.ST];
+    L.mode_blk.assign(N + 1, 0);
+    L.ebo.assign(N + 1, 0);
+    for (int l = 0; l < N; ++l) {
+        const int stlo = l / TS, sthi = std::min((l + N - 1) / TS, L.ST - 1);
+        L.mode_blk[l + 1] = L.mode_blk[l] + (L.bo[sthi + 1] - L.bo[stlo]);
+        const int sta = (2 * l + 1) / TS;
+        L.ebo[l + 1] = L.ebo[l] + (sta <= sthi ? L.bo[sthi + 1] - L.bo[sta] : 0);
+    }
+    L.jblocks = L.mode_blk[N];
+    return L;
+}
+
+// Fills the blocked store of one sample: for mode l and block (st, xt) of its run, entry (r, i) is
+// J of the quadruplet {l, m = s-l, x, s-x} with s = st*TS+r, x = xt*TX+i, or 0 when that is not a
+// quadruplet of distinct modes.
+template <typename real>
+void pack_sample(const SampleLayout &L, const double *J, real *dst) {
+    const int N = L.N;
+    int64_t total;
+    const std::vector<int64_t> off = pair_offsets(N, &total);
+    for (int l = 0; l < N; ++l) {
+        const int stlo = l / TS, sthi = std::min((l + N - 1) / TS, L.ST - 1);
+        int64_t bpos = L.mode_blk[l];
+        for (int b = L.bo[stlo]; b < L.bo[sthi + 1]; ++b, ++bpos) {
+            const int st = (int)(L.blkinfo[b] >> 16), xt = (int)(L.blkinfo[b] & 0xffffu);
+            real *blk = dst + bpos * TBLK;
+            for (int r = 0; r < TS; ++r)
+                for (int i = 0; i < TX; ++i) {
+                    const int s = st * TS + r, x = xt * TX + i, m = s - l, y = s - x;
+                    real v = real(0);
+                    if (m >= 0 && m < N && m != l && s >= 1 && s <= 2 * N - 3 && x >= xlo_of(s, N) &&
+                        x <= xhi_of(s) && x != std::min(l, m)) {
+                        int q[4] = {l, m, x, y};
+                        std::sort(q, q + 4);
+                        const int64_t idx = off[(size_t)q[0] * N + q[1]] + (q[2] - q[1] - 1);
+                        v = (real)J[idx];
+                    }
+                    blk[r * TX + i] = v;
+                }
+        }
+    }
+}
+
+struct SegKey {
+    int seg, n_snap, resync, live, swap;
+    bool operator<(const SegKey &o) const {
+        return std::tie(seg, n_snap, resync, live, swap) < std::tie(o.seg, o.n_snap, o.resync, o.live, o.swap);
+    }
+};
+
+}  // namespace
+
+struct pt_ctx {
+    pt_config cfg;
+    int S = 0, R = 0, nT = 0, maxN = 0;
+    std::vector<int> N;
+    uint64_t seed = 0;
+    bool dbl = false, plain = false;
+    cudaStream_t stream = nullptr;
+    pt_alloc_fn alloc = nullptr;
+    pt_free_fn free_ = nullptr;
+    void *user = nullptr;
+    std::string err;
+    int64_t sweeps_done = 0, swap_passes = 0;
+    int n_chains = 0;
+    int64_t a_total = 0;
+    size_t esize = 8;  // bytes of one real
+    std::vector<SampleDev> samples;
+    std::vector<GroupDev> groups;
+    std::vector<int> chain_sample;
+    std::vector<std::pair<void *, size_t>> allocs;
+    // device buffers
+    SampleDev *d_samples = nullptr;
+    GroupDev *d_groups = nullptr;
+    void *d_J = nullptr;
+    int *d_bo = nullptr, *d_xtlo = nullptr, *d_mode_blk = nullptr, *d_ebo = nullptr;
+    uint32_t *d_blkinfo = nullptr;
+    void *d_a = nullptr;
+    double *d_E = nullptr, *d_beta = nullptr, *d_Etmp = nullptr;
+    int *d_label = nullptr, *d_perm = nullptr, *d_chain_sample = nullptr, *d_progress = nullptr;
+    unsigned long long *d_mc_acc = nullptr, *d_mc_att = nullptr, *d_mcT_acc = nullptr, *d_mcT_att = nullptr;
+    unsigned long long *d_swap_acc = nullptr, *d_swap_att = nullptr, *d_qhist = nullptr;
+    double *d_stat = nullptr, *d_qstat = nullptr, *d_fields = nullptr;
+    Control *d_ctl = nullptr;
+    void *d_snap_a = nullptr;
+    double *d_snap_E = nullptr;
+    int n_snap_max = 0, max_seg = 0;
+    int4 *d_quads = nullptr;
+    double *d_Jq = nullptr;
+    int *d_inc_off = nullptr, *d_inc = nullptr;
+    int G = 8, ncw = 8, spu = 1, grid = 1;
+    std::map<SegKey, cudaGraphExec_t> graphs;
+    std::vector<cudaGraph_t> graph_defs;
+    bool own_stream = false;
+};
+
+namespace {
+
+int fail(pt_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(pt_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, PT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);    \
+    } while (0)
+
+void *dev_alloc(pt_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    void *p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back({p, bytes});
+    return p;
+}
+
+template <typename T> int dalloc(pt_ctx *c, T **out, size_t count) {
+    *out = reinterpret_cast<T *>(dev_alloc(c, count * sizeof(T)));
+    if (!*out) return fail(c, PT_ENOMEM, "device allocation failed");
+    return PT_OK;
+}
+
+template <typename T> int upload(pt_ctx *c, T *dst, const T *src, size_t count) {
+    if (count == 0) return PT_OK;
+    CK(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return PT_OK;
+}
+
+int watchdog_sync(pt_ctx *c) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "device work failed");
+        if (c->cfg.watchdog_ms > 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms > c->cfg.watchdog_ms) return fail(c, PT_ETIMEOUT, "host watchdog: stream did not finish in time");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    Control h;
+    CK(cudaMemcpy(&h, c->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    if (h.error == kErrTimeout) return fail(c, PT_ETIMEOUT, "a bounded device wait ran out (site " + std::to_string(h.error_where) + ")");
+    if (h.error == kErrNaN) return fail(c, PT_ENAN, "non-finite energy or constraint found on the device");
+    if (h.error) return fail(c, PT_ECUDA, "device error status " + std::to_string(h.error));
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------------- kernels
+int run_energy(pt_ctx *c, int renorm, double *E_out, bool write_state) {
+    if (c->plain) {
+        PlainParams p{};
+        p.samples = c->d_samples; p.chain_sample = c->d_chain_sample; p.quads = c->d_quads; p.Jq = c->d_Jq;
+        p.inc_off = c->d_inc_off; p.inc = c->d_inc; p.a = reinterpret_cast<double2 *>(c->d_a); p.E = c->d_E;
+        p.maxN = c->maxN; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl; p.renorm = renorm;
+        p.write_state = write_state ? 1 : 0; p.E_out = E_out;
+        CK(launch_plain_energy(p, c->n_chains, c->stream));
+        return PT_OK;
+    }
+    EnergyParams p{};
+    p.samples = c->d_samples; p.groups = c->d_groups; p.J = c->d_J; p.bo = c->d_bo; p.blkinfo = c->d_blkinfo;
+    p.mode_blk = c->d_mode_blk; p.ebo = c->d_ebo; p.a = c->d_a; p.cc = c->cfg.cc_factor; p.renorm = renorm;
+    p.E_out = E_out; p.E_state = write_state ? c->d_E : nullptr; p.ctl = c->d_ctl;
+    const int Ge = c->dbl ? std::min(c->G, 16) : c->G;
+    CK(launch_energy(c->dbl, Ge, p, (int)c->groups.size(), c->maxN, c->stream));
+    return PT_OK;
+}
+
+int run_measure(pt_ctx *c, int n_snap, int live) {
+    MeasureParams p{};
+    p.samples = c->d_samples; p.a = c->d_a; p.E = c->d_E; p.snap_a = c->d_snap_a; p.snap_E = c->d_snap_E;
+    p.n_snap = n_snap; p.live = live; p.perm = c->d_perm; p.S = c->S; p.R = c->R; p.nT = c->nT;
+    p.dbl = c->dbl ? 1 : 0; p.a_total = c->a_total; p.n_chains = c->n_chains; p.stat = c->d_stat;
+    p.qstat = c->d_qstat; p.qhist = c->d_qhist; p.label = c->d_label;
+    CK(launch_measure(p, c->stream));
+    return PT_OK;
+}
+
+int run_swap(pt_ctx *c) {
+    SwapParams p{};
+    p.samples = c->d_samples; p.E = c->d_E; p.label = c->d_label; p.perm = c->d_perm; p.beta = c->d_beta;
+    p.swap_acc = c->d_swap_acc; p.swap_att = c->d_swap_att; p.mc_acc = c->d_mc_acc; p.mc_att = c->d_mc_att;
+    p.mcT_acc = c->d_mcT_acc; p.mcT_att = c->d_mcT_att; p.S = c->S; p.R = c->R; p.nT = c->nT; p.seed = c->seed;
+    p.ctl = c->d_ctl;
+    CK(launch_swap(p, c->stream));
+    return PT_OK;
+}
+
+int run_sweeps(pt_ctx *c, int seg) {
+    if (c->plain) {
+        PlainParams p{};
+        p.samples = c->d_samples; p.chain_sample = c->d_chain_sample; p.quads = c->d_quads; p.Jq = c->d_Jq;
+        p.inc_off = c->d_inc_off; p.inc = c->d_inc; p.a = reinterpret_cast<double2 *>(c->d_a); p.E = c->d_E;
+        p.label = c->d_label; p.beta = c->d_beta; p.mc_acc = c->d_mc_acc; p.mc_att = c->d_mc_att; p.R = c->R;
+        p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
+        p.n_sweeps = seg; p.measure_every = c->cfg.measure_every;
+        p.snap_a = reinterpret_cast<double2 *>(c->d_snap_a); p.snap_E = c->d_snap_E; p.n_snap_max = c->n_snap_max;
+        p.a_total = c->a_total; p.n_chains = c->n_chains;
+        CK(launch_plain_sweep(p, c->n_chains, c->stream));
+        return PT_OK;
+    }
+    CK(cudaMemsetAsync(c->d_ctl, 0, sizeof(unsigned int), c->stream));  // ticket
+    CK(cudaMemsetAsync(c->d_progress, 0, sizeof(int) * c->groups.size(), c->stream));
+    SweepParams p{};
+    p.samples = c->d_samples; p.groups = c->d_groups; p.n_groups = (int)c->groups.size(); p.J = c->d_J;
+    p.bo = c->d_bo; p.xtlo = c->d_xtlo; p.blkinfo = c->d_blkinfo; p.mode_blk = c->d_mode_blk; p.a = c->d_a;
+    p.E = c->d_E; p.label = c->d_label; p.beta = c->d_beta; p.mc_acc = c->d_mc_acc; p.mc_att = c->d_mc_att;
+    p.R = c->R; p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
+    p.progress = c->d_progress; p.n_sweeps = seg; p.sweeps_per_unit = std::min(c->spu, seg);
+    p.measure_every = c->cfg.measure_every; p.snap_a = c->d_snap_a; p.snap_E = c->d_snap_E;
+    p.n_snap_max = c->n_snap_max; p.a_total = c->a_total; p.n_chains = c->n_chains;
+    const int units = ((seg + p.sweeps_per_unit - 1) / p.sweeps_per_unit) * p.n_groups;
+    const int grid = std::max(1, std::min(c->grid, units));
+    CK(launch_sweep(c->dbl, c->G, c->ncw, p, grid, c->stream));
+    return PT_OK;
+}
+
+// One segment: seg sweeps, then resync / measure / swap as due at its end.
+int enqueue_segment(pt_ctx *c, const SegKey &k) {
+    int rc;
+    if ((rc = run_sweeps(c, k.seg)) != PT_OK) return rc;
+    if (k.resync && (rc = run_energy(c, 1, nullptr, true)) != PT_OK) return rc;
+    if ((k.n_snap || k.live) && (rc = run_measure(c, k.n_snap, k.live)) != PT_OK) return rc;
+    if (k.swap && (rc = run_swap(c)) != PT_OK) return rc;
+    CK(launch_advance(c->d_ctl, k.seg, k.swap ? 1 : 0, c->stream));
+    return PT_OK;
+}
+
+int run_segment(pt_ctx *c, const SegKey &k) {
+    if (!c->cfg.use_graphs) return enqueue_segment(c, k);
+    auto it = c->graphs.find(k);
+    if (it == c->graphs.end()) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        const int rc = enqueue_segment(c, k);
+        cudaGraph_t gg = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &gg);
+        if (rc != PT_OK) {
+            if (gg) cudaGraphDestroy(gg);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+        g = gg;
+        cudaGraphExec_t ex;
+        CK(cudaGraphInstantiate(&ex, g, 0));
+        c->graph_defs.push_back(g);
+        it = c->graphs.emplace(k, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, c->stream));
+    return PT_OK;
+}
+
+void free_all(pt_ctx *c) {
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto g : c->graph_defs) cudaGraphDestroy(g);
+    c->graphs.clear();
+    c->graph_defs.clear();
+    for (auto &p : c->allocs) {
+        if (c->free_) c->free_(p.first, c->user);
+        else cudaFree(p.first);
+    }
+    c->allocs.clear();
+}
+
+}  // namespace
+
+// ================================================================================================ C ABI
+extern "C" {
+
+void pt_config_default(pt_config *cfg) {
+    if (!cfg) return;
+    cfg->precision = PT_PREC_FP32;
+    cfg->cc_factor = 2.0;
+    cfg->swap_every = 64;
+    cfg->measure_every = 16;
+    cfg->resync_every = 64;
+    cfg->chains_per_block = 0;
+    cfg->sweeps_per_unit = 0;
+    cfg->blocks_per_sm = 0;
+    cfg->use_graphs = 1;
+    cfg->watchdog_ms = 600000;
+}
+
+int pt_enumerate_quads(int N, int32_t *abcd, int64_t *count) {
+    if (!count || N < 4 || N > 512) return fail(nullptr, PT_EINVAL, "pt_enumerate_quads: need 4 <= N <= 512 and count");
+    int64_t n = 0;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            for (int c2 = b + 1; c2 < N; ++c2) {
+                const int d = b + c2 - a;
+                if (d >= N) break;
+                if (abcd) {
+                    abcd[4 * n] = a; abcd[4 * n + 1] = b; abcd[4 * n + 2] = c2; abcd[4 * n + 3] = d;
+                }
+                ++n;
+            }
+    *count = n;
+    return PT_OK;
+}
+
+int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const double *J,
+              const int64_t *J_offsets, int n_T, const double *temps, int replicas, uint64_t seed,
+              pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream) {
+    if (!out) return fail(nullptr, PT_EINVAL, "pt_create: out is NULL");
+    *out = nullptr;
+    pt_config cfg;
+    pt_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (S < 1 || !Nv || !J || !J_offsets || n_T < 1 || !temps || replicas < 1)
+        return fail(nullptr, PT_EINVAL, "pt_create: need S >= 1, N, J, J_offsets, n_T >= 1, temps, replicas >= 1");
+    if ((alloc == nullptr) != (free_ == nullptr)) return fail(nullptr, PT_EINVAL, "pt_create: give both alloc and free or neither");
+    if (cfg.precision < PT_PREC_FP32 || cfg.precision > PT_PREC_FP64_PLAIN) return fail(nullptr, PT_EINVAL, "pt_create: bad precision");
+    if (!(cfg.cc_factor > 0.0) || !std::isfinite(cfg.cc_factor)) return fail(nullptr, PT_EINVAL, "pt_create: cc_factor must be positive");
+    if (cfg.swap_every < 0 || cfg.measure_every < 0 || cfg.resync_every < 0)
+        return fail(nullptr, PT_EINVAL, "pt_create: negative schedule interval");
+    for (int t = 0; t < n_T; ++t) {
+        if (!(temps[t] > 0.0) || !std::isfinite(temps[t])) return fail(nullptr, PT_EINVAL, "pt_create: temperatures must be positive");
+        if (t && !(temps[t] > temps[t - 1])) return fail(nullptr, PT_EINVAL, "pt_create: temperatures must be strictly ascending");
+    }
+    if ((int64_t)S * replicas * n_T > (1ll << 28)) return fail(nullptr, PT_EINVAL, "pt_create: too many chains");
+    for (int s = 0; s < S; ++s) {
+        if (Nv[s] < 4 || Nv[s] > 512 || (Nv[s] & 1)) return fail(nullptr, PT_EINVAL, "pt_create: every N must be even, 4..512");
+        int64_t nq;
+        pt_enumerate_quads(Nv[s], nullptr, &nq);
+        if (J_offsets[s + 1] - J_offsets[s] != nq) return fail(nullptr, PT_EINVAL, "pt_create: J_offsets do not match the quadruplet counts");
+        for (int64_t i = J_offsets[s]; i < J_offsets[s + 1]; ++i)
+            if (!std::isfinite(J[i])) return fail(nullptr, PT_ENAN, "pt_create: non-finite coupling");
+    }
+    pt_ctx *c = new pt_ctx();
+    c->cfg = cfg;
+    c->S = S; c->R = replicas; c->nT = n_T; c->seed = seed;
+    c->N.assign(Nv, Nv + S);
+    c->maxN = *std::max_element(c->N.begin(), c->N.end());
+    c->dbl = cfg.precision != PT_PREC_FP32;
+    c->plain = cfg.precision == PT_PREC_FP64_PLAIN;
+    c->esize = c->dbl ? 8 : 4;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->alloc = alloc; c->free_ = free_; c->user = alloc_user;
+    if (c->stream == nullptr) {
+        // the legacy default stream cannot be captured into graphs: run on a stream of our own
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            delete c;
+            return fail(nullptr, PT_ECUDA, "pt_create: cannot create a CUDA stream");
+        }
+        c->own_stream = true;
+    }
+    auto bail = [&](int rc) {
+        g_create_error = c->err;
+        free_all(c);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return rc;
+    };
+#undef CK
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, #call));      \
+    } while (0)
+#define RC(x)                          \
+    do {                               \
+        int r_ = (x);                  \
+        if (r_ != PT_OK) return bail(r_); \
+    } while (0)
+
+    // ---- scheduling shape
+    const int chains_ps = replicas * n_T;
+    int G = cfg.chains_per_block, ncw = 8;
+    if (G == 0) {
+        if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
+        else G = (c->maxN >= 128) ? 8 : (c->maxN >= 48 ? 16 : 32);
+        if (G > 8 && chains_ps <= 8) G = 8;
+    }
+    if (c->dbl) ncw = (G == 16) ? 4 : 8;
+    else ncw = (G == 8) ? 8 : (G == 16 ? 8 : 4);
+    if (!c->plain && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
+    c->G = G; c->ncw = ncw;
+    c->spu = cfg.sweeps_per_unit > 0 ? cfg.sweeps_per_unit
+                                     : (c->maxN >= 192 ? 1 : c->maxN >= 96 ? 2 : c->maxN >= 48 ? 8 : 32);
+
+    // ---- samples, chains, groups, layouts
+    std::vector<SampleLayout> lay(S);
+    std::vector<int> bo_all, xtlo_all, mode_all, ebo_all;
+    std::vector<uint32_t> binfo_all;
+    int64_t jblocks = 0, a_off = 0, q_off = 0, inc_total = 0;
+    int chain0 = 0;
+    for (int s = 0; s < S; ++s) {
+        lay[s] = make_layout(c->N[s]);
+        SampleDev sd{};
+        sd.N = c->N[s]; sd.ST = lay[s].ST; sd.nblk = lay[s].nblk; sd.chains = chains_ps; sd.chain0 = chain0;
+        sd.tab_off = (int)bo_all.size(); sd.blk_off = (int)binfo_all.size(); sd.mode_off = (int)mode_all.size();
+        sd.J_off = jblocks; sd.a_off = a_off; sd.q_off = q_off; sd.nq = J_offsets[s + 1] - J_offsets[s];
+        sd.inc_off = inc_total;
+        bo_all.insert(bo_all.end(), lay[s].bo.begin(), lay[s].bo.end());
+        xtlo_all.insert(xtlo_all.end(), lay[s].xtlo.begin(), lay[s].xtlo.end());
+        xtlo_all.push_back(0);
+        binfo_all.insert(binfo_all.end(), lay[s].blkinfo.begin(), lay[s].blkinfo.end());
+        mode_all.insert(mode_all.end(), lay[s].mode_blk.begin(), lay[s].mode_blk.end());
+        ebo_all.insert(ebo_all.end(), lay[s].ebo.begin(), lay[s].ebo.end());
+        c->samples.push_back(sd);
+        for (int i = 0; i < chains_ps; ++i) c->chain_sample.push_back(s);
+        for (int g0 = 0; g0 < chains_ps; g0 += G) c->groups.push_back({s, chain0 + g0, std::min(G, chains_ps - g0), 0});
+        jblocks += lay[s].jblocks;
+        a_off += (int64_t)c->N[s] * chains_ps;
+        q_off += sd.nq;
+        inc_total += 4 * sd.nq;
+        chain0 += chains_ps;
+    }
+    // xtlo needs ST entries per sample at tab_off; pad to keep offsets aligned with bo (ST+1 entries)
+    c->n_chains = chain0;
+    c->a_total = a_off;
+    // expensive groups first (ragged batches): cost ~ N^3
+    std::stable_sort(c->groups.begin(), c->groups.end(), [&](const GroupDev &x, const GroupDev &y) {
+        return c->N[x.sample] > c->N[y.sample];
+    });
+
+    // ---- schedule buffers
+    int ev = 0;
+    for (int e : {cfg.swap_every, cfg.resync_every}) if (e > 0) ev = ev ? std::min(ev, e) : e;
+    c->max_seg = ev ? ev : 256;
+    c->n_snap_max = cfg.measure_every > 0 ? std::max(1, (c->max_seg + cfg.measure_every - 1) / cfg.measure_every) : 1;
+
+    // ---- device memory
+    RC(dalloc(c, &c->d_samples, S));
+    RC(dalloc(c, &c->d_groups, c->groups.size()));
+    RC(dalloc(c, &c->d_bo, bo_all.size()));
+    RC(dalloc(c, &c->d_xtlo, xtlo_all.size()));
+    RC(dalloc(c, &c->d_blkinfo, std::max<size_t>(1, binfo_all.size())));
+    RC(dalloc(c, &c->d_mode_blk, mode_all.size()));
+    RC(dalloc(c, &c->d_ebo, ebo_all.size()));
+    c->d_a = dev_alloc(c, (size_t)c->a_total * 2 * c->esize);
+    if (!c->d_a) return bail(fail(c, PT_ENOMEM, "device allocation failed (state)"));
+    c->d_snap_a = dev_alloc(c, (size_t)c->n_snap_max * c->a_total * 2 * c->esize);
+    if (!c->d_snap_a) return bail(fail(c, PT_ENOMEM, "device allocation failed (snapshots)"));
+    RC(dalloc(c, &c->d_snap_E, (size_t)c->n_snap_max * c->n_chains));
+    RC(dalloc(c, &c->d_E, c->n_chains));
+    RC(dalloc(c, &c->d_Etmp, c->n_chains));
+    RC(dalloc(c, &c->d_beta, n_T));
+    RC(dalloc(c, &c->d_label, c->n_chains));
+    RC(dalloc(c, &c->d_perm, c->n_chains));
+    RC(dalloc(c, &c->d_chain_sample, c->n_chains));
+    RC(dalloc(c, &c->d_progress, c->groups.size()));
+    RC(dalloc(c, &c->d_mc_acc, c->n_chains));
+    RC(dalloc(c, &c->d_mc_att, c->n_chains));
+    RC(dalloc(c, &c->d_mcT_acc, (size_t)S * n_T));
+    RC(dalloc(c, &c->d_mcT_att, (size_t)S * n_T));
+    const size_t npair = (size_t)S * replicas * std::max(1, n_T - 1);
+    RC(dalloc(c, &c->d_swap_acc, npair));
+    RC(dalloc(c, &c->d_swap_att, npair));
+    RC(dalloc(c, &c->d_qhist, (size_t)S * n_T * PT_QBINS));
+    RC(dalloc(c, &c->d_stat, (size_t)S * n_T * PT_NSTAT));
+    RC(dalloc(c, &c->d_qstat, (size_t)S * n_T * PT_NQSTAT));
+    RC(dalloc(c, &c->d_fields, (size_t)chains_ps * 8));
+    RC(dalloc(c, &c->d_ctl, 1));
+
+    // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
+    if (!c->plain) {
+        c->d_J = dev_alloc(c, (size_t)jblocks * TBLK * c->esize);
+        if (!c->d_J) return bail(fail(c, PT_ENOMEM, "device allocation failed (couplings)"));
+        std::vector<unsigned char> hJ((size_t)jblocks * TBLK * c->esize);
+        for (int s = 0; s < S; ++s) {
+            if (c->dbl) pack_sample<double>(lay[s], J + J_offsets[s], reinterpret_cast<double *>(hJ.data()) + c->samples[s].J_off * TBLK);
+            else pack_sample<float>(lay[s], J + J_offsets[s], reinterpret_cast<float *>(hJ.data()) + c->samples[s].J_off * TBLK);
+        }
+        CK(cudaMemcpy(c->d_J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<int4> hq((size_t)std::max<int64_t>(q_off, 1));
+        std::vector<double> hJq((size_t)std::max<int64_t>(q_off, 1));
+        std::vector<int> hinc_off, hinc((size_t)std::max<int64_t>(inc_total, 1));
+        for (int s = 0; s < S; ++s) {
+            const int n = c->N[s];
+            const SampleDev &sd = c->samples[s];
+            std::vector<int32_t> abcd((size_t)4 * std::max<int64_t>(sd.nq, 1));
+            int64_t cnt;
+            pt_enumerate_quads(n, abcd.data(), &cnt);
+            std::vector<int> deg(n + 1, 0);
+            for (int64_t q = 0; q < cnt; ++q) {
+                hq[sd.q_off + q] = make_int4(abcd[4 * q], abcd[4 * q + 1], abcd[4 * q + 2], abcd[4 * q + 3]);
+                hJq[sd.q_off + q] = J[J_offsets[s] + q];
+                for (int m = 0; m < 4; ++m) deg[abcd[4 * q + m] + 1]++;
+            }
+            for (int l = 0; l < n; ++l) deg[l + 1] += deg[l];
+            std::vector<int> fill(n, 0);
+            for (int64_t q = 0; q < cnt; ++q)
+                for (int m = 0; m < 4; ++m) {
+                    const int l = abcd[4 * q + m];
+                    hinc[sd.inc_off + deg[l] + fill[l]++] = (int)q;
+                }
+            hinc_off.insert(hinc_off.end(), deg.begin(), deg.end());
+        }
+        RC(dalloc(c, &c->d_quads, hq.size()));
+        RC(dalloc(c, &c->d_Jq, hJq.size()));
+        RC(dalloc(c, &c->d_inc_off, hinc_off.size()));
+        RC(dalloc(c, &c->d_inc, hinc.size()));
+        CK(cudaMemcpy(c->d_quads, hq.data(), hq.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_Jq, hJq.data(), hJq.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_inc_off, hinc_off.data(), hinc_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_inc, hinc.data(), hinc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    std::vector<int> label(c->n_chains), perm(c->n_chains);
+    for (int s = 0; s < S; ++s)
+        for (int r = 0; r < replicas; ++r)
+            for (int t = 0; t < n_T; ++t) {
+                const int slot = c->samples[s].chain0 + r * n_T + t;
+                label[slot] = t;
+                perm[((size_t)s * replicas + r) * n_T + t] = slot;
+            }
+    std::vector<double> beta(n_T);
+    for (int t = 0; t < n_T; ++t) beta[t] = 1.0 / temps[t];
+    CK(cudaMemcpy(c->d_samples, c->samples.data(), S * sizeof(SampleDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_groups, c->groups.data(), c->groups.size() * sizeof(GroupDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_bo, bo_all.data(), bo_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_xtlo, xtlo_all.data(), xtlo_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!binfo_all.empty()) CK(cudaMemcpy(c->d_blkinfo, binfo_all.data(), binfo_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_mode_blk, mode_all.data(), mode_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_ebo, ebo_all.data(), ebo_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_label, label.data(), label.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_chain_sample, c->chain_sample.data(), c->chain_sample.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_beta, beta.data(), n_T * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->d_mc_acc, 0, c->n_chains * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_mc_att, 0, c->n_chains * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_mcT_acc, 0, (size_t)S * n_T * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_mcT_att, 0, (size_t)S * n_T * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_swap_acc, 0, npair * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_swap_att, 0, npair * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_qhist, 0, (size_t)S * n_T * PT_QBINS * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_stat, 0, (size_t)S * n_T * PT_NSTAT * sizeof(double)));
+    CK(cudaMemset(c->d_qstat, 0, (size_t)S * n_T * PT_NQSTAT * sizeof(double)));
+    CK(cudaMemset(c->d_ctl, 0, sizeof(Control)));
+
+    // ---- persistent grid
+    if (!c->plain) {
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int occ = sweep_occupancy(c->dbl, G, ncw, c->maxN);
+        if (occ < 1) return bail(fail(c, PT_EUNSUPPORTED, "pt_create: sweep kernel does not fit on this GPU for this N"));
+        const int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
+        c->grid = std::max(1, std::min((int)c->groups.size(), sms * bps));
+    }
+
+    // ---- initial chains (exact beta = 0 draws) and their energies
+    InitParams ip{};
+    ip.samples = c->d_samples; ip.chain_sample = c->d_chain_sample; ip.label = c->d_label; ip.a = c->d_a;
+    ip.dbl = c->dbl ? 1 : 0; ip.R = replicas; ip.nT = n_T; ip.seed = seed;
+    CK(launch_init(ip, c->n_chains, c->stream));
+    RC(run_energy(c, 0, nullptr, true));
+    RC(watchdog_sync(c));
+#undef CK
+#undef RC
+    *out = c;
+    return PT_OK;
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);    \
+    } while (0)
+
+int pt_sweep(pt_ctx *c, int64_t n) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_sweep: NULL context");
+    if (n < 0) return fail(c, PT_EINVAL, "pt_sweep: negative sweep count");
+    const pt_config &cf = c->cfg;
+    while (n > 0) {
+        const int64_t d = c->sweeps_done;
+        int64_t nb = d + c->max_seg;
+        for (int e : {cf.swap_every, cf.resync_every})
+            if (e > 0) nb = std::min(nb, (d / e + 1) * e);
+        const int seg = (int)std::min<int64_t>(n, nb - d);
+        const int64_t end = d + seg;
+        SegKey k{};
+        k.seg = seg;
+        k.n_snap = 0;
+        if (cf.measure_every > 0) {
+            const int64_t me = cf.measure_every;
+            k.n_snap = (int)((end - 1) / me - d / me);  // measurement points in (d, end)
+            k.live = (end % me == 0) ? 1 : 0;
+        }
+        k.resync = (cf.resync_every > 0 && end % cf.resync_every == 0) ? 1 : 0;
+        k.swap = (cf.swap_every > 0 && end % cf.swap_every == 0 && c->nT > 1) ? 1 : 0;
+        if (k.n_snap > c->n_snap_max) return fail(c, PT_EINVAL, "pt_sweep: internal snapshot overflow");
+        // a graph replays fixed sweep indices relative to the device counters: only the
+        // segment shape enters the key
+        const int rc = run_segment(c, k);
+        if (rc != PT_OK) return rc;
+        c->sweeps_done = end;
+        c->swap_passes += k.swap;
+        n -= seg;
+    }
+    return PT_OK;
+}
+
+int pt_swap(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_swap: NULL context");
+    if (c->nT < 2) return PT_OK;
+    const int rc = run_swap(c);
+    if (rc != PT_OK) return rc;
+    CK(launch_advance(c->d_ctl, 0, 1, c->stream));
+    c->swap_passes++;
+    return PT_OK;
+}
+
+int pt_resync(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_resync: NULL context");
+    return run_energy(c, 1, nullptr, true);
+}
+
+int pt_measure_now(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_measure_now: NULL context");
+    return run_measure(c, 0, 1);
+}
+
+int pt_measure(pt_ctx *c, pt_observables *o) {
+    if (!c || !o) return fail(c, PT_EINVAL, "pt_measure: NULL argument");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    const size_t ST = (size_t)c->S * c->nT, npair = (size_t)c->S * c->R * std::max(1, c->nT - 1);
+    if (o->stat) CK(cudaMemcpy(o->stat, c->d_stat, ST * PT_NSTAT * sizeof(double), cudaMemcpyDeviceToHost));
+    if (o->qstat) CK(cudaMemcpy(o->qstat, c->d_qstat, ST * PT_NQSTAT * sizeof(double), cudaMemcpyDeviceToHost));
+    if (o->qhist) CK(cudaMemcpy(o->qhist, c->d_qhist, ST * PT_QBINS * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (o->swap_acc) CK(cudaMemcpy(o->swap_acc, c->d_swap_acc, npair * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (o->swap_att) CK(cudaMemcpy(o->swap_att, c->d_swap_att, npair * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (o->mc_acc || o->mc_att) {
+        std::vector<unsigned long long> ta(ST), tt(ST), ca(c->n_chains), ct(c->n_chains);
+        std::vector<int> lab(c->n_chains);
+        CK(cudaMemcpy(ta.data(), c->d_mcT_acc, ST * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tt.data(), c->d_mcT_att, ST * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ca.data(), c->d_mc_acc, c->n_chains * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ct.data(), c->d_mc_att, c->n_chains * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(lab.data(), c->d_label, c->n_chains * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int slot = 0; slot < c->n_chains; ++slot) {
+            const size_t i = (size_t)c->chain_sample[slot] * c->nT + lab[slot];
+            ta[i] += ca[slot];
+            tt[i] += ct[slot];
+        }
+        if (o->mc_acc) std::memcpy(o->mc_acc, ta.data(), ST * sizeof(uint64_t));
+        if (o->mc_att) std::memcpy(o->mc_att, tt.data(), ST * sizeof(uint64_t));
+    }
+    return PT_OK;
+}
+
+int pt_reset_observables(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_reset_observables: NULL context");
+    const size_t ST = (size_t)c->S * c->nT, npair = (size_t)c->S * c->R * std::max(1, c->nT - 1);
+    CK(cudaMemsetAsync(c->d_stat, 0, ST * PT_NSTAT * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->d_qstat, 0, ST * PT_NQSTAT * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->d_qhist, 0, ST * PT_QBINS * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_swap_acc, 0, npair * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_swap_att, 0, npair * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_mcT_acc, 0, ST * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_mcT_att, 0, ST * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_mc_acc, 0, c->n_chains * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_mc_att, 0, c->n_chains * sizeof(uint64_t), c->stream));
+    return PT_OK;
+}
+
+// canonical index of every chain slot: (s, r, label)
+static int canonical_map(pt_ctx *c, std::vector<int> &canon) {
+    std::vector<int> lab(c->n_chains);
+    CK(cudaMemcpy(lab.data(), c->d_label, c->n_chains * sizeof(int), cudaMemcpyDeviceToHost));
+    canon.resize(c->n_chains);
+    for (int slot = 0; slot < c->n_chains; ++slot) {
+        const int s = c->chain_sample[slot];
+        const int r = (slot - c->samples[s].chain0) / c->nT;
+        canon[slot] = c->samples[s].chain0 + r * c->nT + lab[slot];
+    }
+    return PT_OK;
+}
+
+int pt_get_state(pt_ctx *c, double *a, double *E) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_get_state: NULL context");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    std::vector<int> canon;
+    if ((rc = canonical_map(c, canon)) != PT_OK) return rc;
+    if (a) {
+        std::vector<unsigned char> h((size_t)c->a_total * 2 * c->esize);
+        CK(cudaMemcpy(h.data(), c->d_a, h.size(), cudaMemcpyDeviceToHost));
+        for (int slot = 0; slot < c->n_chains; ++slot) {
+            const SampleDev &sd = c->samples[c->chain_sample[slot]];
+            const int64_t src = sd.a_off + (int64_t)(slot - sd.chain0) * sd.N;
+            const int64_t dst = sd.a_off + (int64_t)(canon[slot] - sd.chain0) * sd.N;
+            for (int x = 0; x < 2 * sd.N; ++x)
+                a[2 * dst + x] = c->dbl ? reinterpret_cast<double *>(h.data())[2 * src + x]
+                                        : (double)reinterpret_cast<float *>(h.data())[2 * src + x];
+        }
+    }
+    if (E) {
+        std::vector<double> h(c->n_chains);
+        CK(cudaMemcpy(h.data(), c->d_E, c->n_chains * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int slot = 0; slot < c->n_chains; ++slot) E[canon[slot]] = h[slot];
+    }
+    return PT_OK;
+}
+
+int pt_set_state(pt_ctx *c, const double *a) {
+    if (!c || !a) return fail(c, PT_EINVAL, "pt_set_state: NULL argument");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    std::vector<int> canon;
+    if ((rc = canonical_map(c, canon)) != PT_OK) return rc;
+    std::vector<unsigned char> h((size_t)c->a_total * 2 * c->esize);
+    for (int slot = 0; slot < c->n_chains; ++slot) {
+        const SampleDev &sd = c->samples[c->chain_sample[slot]];
+        const int64_t dst = sd.a_off + (int64_t)(slot - sd.chain0) * sd.N;
+        const int64_t src = sd.a_off + (int64_t)(canon[slot] - sd.chain0) * sd.N;
+        for (int x = 0; x < 2 * sd.N; ++x) {
+            const double v = a[2 * src + x];
+            if (!std::isfinite(v)) return fail(c, PT_ENAN, "pt_set_state: non-finite amplitude");
+            if (c->dbl) reinterpret_cast<double *>(h.data())[2 * dst + x] = v;
+            else reinterpret_cast<float *>(h.data())[2 * dst + x] = (float)v;
+        }
+    }
+    CK(cudaMemcpyAsync(c->d_a, h.data(), h.size(), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = run_energy(c, 0, nullptr, true)) != PT_OK) return rc;
+    return watchdog_sync(c);
+}
+
+int pt_energy(pt_ctx *c, double *E) {
+    if (!c || !E) return fail(c, PT_EINVAL, "pt_energy: NULL argument");
+    int rc = run_energy(c, 0, c->d_Etmp, false);
+    if (rc != PT_OK) return rc;
+    if ((rc = watchdog_sync(c)) != PT_OK) return rc;
+    std::vector<int> canon;
+    if ((rc = canonical_map(c, canon)) != PT_OK) return rc;
+    std::vector<double> h(c->n_chains);
+    CK(cudaMemcpy(h.data(), c->d_Etmp, c->n_chains * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int slot = 0; slot < c->n_chains; ++slot) E[canon[slot]] = h[slot];
+    return PT_OK;
+}
+
+int pt_fields(pt_ctx *c, int sample, int j, int k, double *out) {
+    if (!c || !out) return fail(c, PT_EINVAL, "pt_fields: NULL argument");
+    if (c->plain) return fail(c, PT_EUNSUPPORTED, "pt_fields: not available for the plain FP64 path");
+    if (sample < 0 || sample >= c->S) return fail(c, PT_EINVAL, "pt_fields: bad sample");
+    const int N = c->N[sample];
+    if (j < 0 || j >= N || k < 0 || k >= N || j == k) return fail(c, PT_EINVAL, "pt_fields: need distinct modes in [0, N)");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    // the groups of one sample are contiguous (a stable sort by N keeps sample order within equal N)
+    int g0 = -1, ng = 0;
+    for (size_t i = 0; i < c->groups.size(); ++i)
+        if (c->groups[i].sample == sample) { if (g0 < 0) g0 = (int)i; ++ng; }
+    FieldsParams p{};
+    p.samples = c->d_samples; p.groups = c->d_groups; p.group0 = g0; p.J = c->d_J; p.bo = c->d_bo;
+    p.blkinfo = c->d_blkinfo; p.mode_blk = c->d_mode_blk; p.a = c->d_a; p.j = j; p.k = k; p.out = c->d_fields;
+    const int Gf = c->dbl ? std::min(c->G, 16) : c->G;
+    cudaError_t e = launch_fields(c->dbl, Gf, p, ng, c->maxN, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pt_fields");
+    const int cps = c->R * c->nT;
+    std::vector<double> h((size_t)cps * 8);
+    CK(cudaMemcpy(h.data(), c->d_fields, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<int> canon;
+    if ((rc = canonical_map(c, canon)) != PT_OK) return rc;
+    const int c0 = c->samples[sample].chain0;
+    for (int i = 0; i < cps; ++i) {
+        const int dst = canon[c0 + i] - c0;
+        for (int e2 = 0; e2 < 8; ++e2) out[(size_t)dst * 8 + e2] = h[(size_t)i * 8 + e2];
+    }
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------------- checkpoints
+namespace {
+const char kMagic[8] = {'P', 'T', 'G', 'B', 'C', 'K', 'P', '1'};
+struct CkptHeader {
+    char magic[8];
+    int32_t version, S, R, nT, precision, n_chains;
+    int64_t a_total, sweeps_done, swap_passes;
+    uint64_t seed, layout_hash;
+};
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+uint64_t layout_hash(const pt_ctx *c) {
+    uint64_t h = fnv1a(reinterpret_cast<const unsigned char *>(c->N.data()), c->N.size() * sizeof(int));
+    return fnv1a(reinterpret_cast<const unsigned char *>(&c->cfg.cc_factor), sizeof(double), h);
+}
+struct Blob { void *dev; size_t bytes; };
+std::vector<Blob> blobs(pt_ctx *c) {
+    const size_t ST = (size_t)c->S * c->nT, npair = (size_t)c->S * c->R * std::max(1, c->nT - 1);
+    return {{c->d_a, (size_t)c->a_total * 2 * c->esize},
+            {c->d_E, c->n_chains * sizeof(double)},
+            {c->d_label, c->n_chains * sizeof(int)},
+            {c->d_perm, c->n_chains * sizeof(int)},
+            {c->d_mc_acc, c->n_chains * sizeof(uint64_t)},
+            {c->d_mc_att, c->n_chains * sizeof(uint64_t)},
+            {c->d_mcT_acc, ST * sizeof(uint64_t)},
+            {c->d_mcT_att, ST * sizeof(uint64_t)},
+            {c->d_stat, ST * PT_NSTAT * sizeof(double)},
+            {c->d_qstat, ST * PT_NQSTAT * sizeof(double)},
+            {c->d_qhist, ST * PT_QBINS * sizeof(uint64_t)},
+            {c->d_swap_acc, npair * sizeof(uint64_t)},
+            {c->d_swap_att, npair * sizeof(uint64_t)}};
+}
+}  // namespace
+
+int pt_save(pt_ctx *c, void *buf, size_t *len) {
+    if (!c || !len) return fail(c, PT_EINVAL, "pt_save: NULL argument");
+    auto bl = blobs(c);
+    size_t need = sizeof(CkptHeader) + sizeof(uint64_t);
+    for (auto &b : bl) need += b.bytes;
+    if (!buf) { *len = need; return PT_OK; }
+    if (*len < need) return fail(c, PT_EINVAL, "pt_save: buffer too small");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    unsigned char *p = reinterpret_cast<unsigned char *>(buf);
+    CkptHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1; h.S = c->S; h.R = c->R; h.nT = c->nT; h.precision = c->cfg.precision; h.n_chains = c->n_chains;
+    h.a_total = c->a_total; h.sweeps_done = c->sweeps_done; h.swap_passes = c->swap_passes; h.seed = c->seed;
+    h.layout_hash = layout_hash(c);
+    std::memcpy(p, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (auto &b : bl) {
+        CK(cudaMemcpy(p + off, b.dev, b.bytes, cudaMemcpyDeviceToHost));
+        off += b.bytes;
+    }
+    const uint64_t sum = fnv1a(p, off);
+    std::memcpy(p + off, &sum, sizeof(sum));
+    *len = need;
+    return PT_OK;
+}
+
+int pt_load(pt_ctx *c, const void *buf, size_t len) {
+    if (!c || !buf) return fail(c, PT_EINVAL, "pt_load: NULL argument");
+    auto bl = blobs(c);
+    size_t need = sizeof(CkptHeader) + sizeof(uint64_t);
+    for (auto &b : bl) need += b.bytes;
+    if (len != need) return fail(c, PT_ESTATE, "pt_load: checkpoint size does not match this context");
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(buf);
+    CkptHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(c, PT_ESTATE, "pt_load: not a checkpoint");
+    if (h.S != c->S || h.R != c->R || h.nT != c->nT || h.precision != c->cfg.precision || h.n_chains != c->n_chains ||
+        h.a_total != c->a_total || h.seed != c->seed || h.layout_hash != layout_hash(c))
+        return fail(c, PT_ESTATE, "pt_load: checkpoint belongs to a different context");
+    uint64_t sum;
+    std::memcpy(&sum, p + need - sizeof(sum), sizeof(sum));
+    if (fnv1a(p, need - sizeof(sum)) != sum) return fail(c, PT_ESTATE, "pt_load: checksum mismatch");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    size_t off = sizeof(h);
+    for (auto &b : bl) {
+        CK(cudaMemcpy(b.dev, p + off, b.bytes, cudaMemcpyHostToDevice));
+        off += b.bytes;
+    }
+    Control ctl{};
+    ctl.sweep_base = h.sweeps_done;
+    ctl.swap_passes = h.swap_passes;
+    CK(cudaMemcpy(c->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
+    c->sweeps_done = h.sweeps_done;
+    c->swap_passes = h.swap_passes;
+    return PT_OK;
+}
+
+int pt_counters(pt_ctx *c, int64_t *sweeps_done, int64_t *swap_passes) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_counters: NULL context");
+    if (sweeps_done) *sweeps_done = c->sweeps_done;
+    if (swap_passes) *swap_passes = c->swap_passes;
+    return PT_OK;
+}
+
+int pt_sync(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_sync: NULL context");
+    return watchdog_sync(c);
+}
+
+int pt_destroy(pt_ctx *c) {
+    if (!c) return PT_OK;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PT_OK;
+}
+
+const char *pt_last_error(const pt_ctx *c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

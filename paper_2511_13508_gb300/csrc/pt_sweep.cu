@@ -1,0 +1,847 @@
+// pt_sweep.cu -- the J-sharing Metropolis sweep kernel (sm_103a), its field-only twin and the
+// full-energy (resync) kernel, for the smoothed-cubic 4-body random-laser model (arXiv 2511.13508).
+//
+// Local field of the updated modes (paper Sec. III.A.3).  With z_P = a_x a_y for the pair P = {x,y},
+// the field of mode l factorises over the pair sum s = x + y:
+//     h_l = sum_s conj(a_{s-l}) acc_l[s],     acc_l[s] = sum_{P : x+y=s} J_l[s][P] z_P,
+// where J_l[s][P] is the coupling of quadruplet {l, s-l} u P.  One pair product z_P therefore feeds
+// both fields of a pair update (j,k), and all chains of a disorder sample read J_j and J_k once per
+// thread block: the J rows stream HBM/L2 -> shared memory through cp.async.bulk (TMA) into a ring of
+// stages, guarded by mbarriers, while the chains' amplitudes stay resident in shared memory.
+//
+// Delta H of a pair move (j,k) (Sec. III.A.1; cross term = reading R5 of the design notes):
+//     dH = -cc Re[ conj(dj) h_j + conj(dk) h_k + conj(dj) dk B_jk + conj(dj) conj(dk) A_jk ],
+//     B_jk = sum_s conj(a_{s-j}) J_j[s][{k, s-k}] a_{s-k},   A_jk = acc_j[j+k].
+#include <cstdint>
+#include <cstdio>
+#include "pt_common.cuh"
+#include "pt_kernels.h"
+
+namespace ptgb {
+
+// ------------------------------------------------------------------------------------------------
+// PTX wrappers: mbarrier, bulk copy, named barriers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after kWaitNs of wall time, records the error and reports failure.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, Control *ctl, int where,
+                                                  volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((n & 63u) == 0 && global_ns() - t0 > kWaitNs) {
+            record_error(ctl, kErrTimeout, where);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ------------------------------------------------------------------------------------------------
+// complex arithmetic on float2/double2
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {  // conj(a) * b
+    V r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
+}
+template <typename V, typename T> __device__ __forceinline__ void caxpy(V &acc, T s, V z) {
+    acc.x = fma(s, z.x, acc.x);
+    acc.y = fma(s, z.y, acc.y);
+}
+template <typename V> __device__ __forceinline__ void cadd(V &acc, V z) { acc.x += z.x; acc.y += z.y; }
+
+// Row-stride of the shared amplitude table [x + APAD][chain] (complex elements): one pad element for
+// 8-byte complex with 8 chains, so that four workers reading rows 8 apart hit distinct bank halves.
+template <typename real, int G> struct RowStride {
+    static constexpr int value = (sizeof(real) == 4 && G == 8) ? G + 1 : G;
+};
+
+// Loads one J row (TX reals) of a block as vectors.
+template <typename real> struct JRow;
+template <> struct JRow<float> {
+    float v[TX];
+    __device__ __forceinline__ void load(const float *p) {
+        const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+template <> struct JRow<double> {
+    double v[TX];
+    __device__ __forceinline__ void load(const double *p) {
+#pragma unroll
+        for (int i = 0; i < TX; i += 2) {
+            const double2 a = *reinterpret_cast<const double2 *>(p + i);
+            v[i] = a.x; v[i + 1] = a.y;
+        }
+    }
+};
+
+// Per-lane partial sums of one pair update.
+template <typename real> struct Partials {
+    typename vec2<real>::type hj, hk, B, A;
+    __device__ __forceinline__ void zero() {
+        hj.x = hj.y = hk.x = hk.y = B.x = B.y = A.x = A.y = real(0);
+    }
+};
+
+// One TS x TX block of pair products for chain c: accumulates the j field (MODE & 1), the k field
+// (MODE & 2), and the j-k cross terms (with the j field).  as = shared amplitude table.
+template <typename real, int RS, int MODE>
+__device__ __forceinline__ void process_block(const typename vec2<real>::type *__restrict__ as, int c, int s0,
+                                              int x0, int j, int k, int N, const real *Jj, const real *Jk,
+                                              Partials<real> &p) {
+    using V = typename vec2<real>::type;
+    V ax[TX], ay[TS + TX - 1];
+#pragma unroll
+    for (int i = 0; i < TX; ++i) ax[i] = as[(x0 + i + APAD) * RS + c];
+    const int ybase = s0 - x0 - (TX - 1) + APAD;
+#pragma unroll
+    for (int d = 0; d < TS + TX - 1; ++d) ay[d] = as[(ybase + d) * RS + c];
+#pragma unroll
+    for (int r = 0; r < TS; ++r) {
+        V accj, acck;
+        accj.x = accj.y = acck.x = acck.y = real(0);
+        JRow<real> rj, rk;
+        if (MODE & 1) rj.load(Jj + r * TX);
+        if (MODE & 2) rk.load(Jk + r * TX);
+#pragma unroll
+        for (int i = 0; i < TX; ++i) {
+            const V z = cmul(ax[i], ay[r - i + TX - 1]);
+            if (MODE & 1) caxpy(accj, rj.v[i], z);
+            if (MODE & 2) caxpy(acck, rk.v[i], z);
+        }
+        const int s = s0 + r;
+        if (MODE & 1) {
+            const V m = as[(s - j + APAD) * RS + c];
+            cadd(p.hj, cmulc(m, accj));
+            if (s == j + k) cadd(p.A, accj);
+        }
+        if (MODE & 2) {
+            const V m = as[(s - k + APAD) * RS + c];
+            cadd(p.hk, cmulc(m, acck));
+        }
+    }
+    if (MODE & 1) {
+        // B_jk: the element of row s at x* = min(k, s-k) belongs to this block for the rows s >= 2k of
+        // the column tile holding k, and for the rows s - k in [x0, x0+TX) of the diagonal band.
+        const bool col = (k >= x0 && k < x0 + TX);
+        const bool diag = (s0 + TS - 1 >= x0 + k) && (s0 <= x0 + TX - 1 + k);
+        if (col || diag) {
+#pragma unroll
+            for (int r = 0; r < TS; ++r) {
+                const int s = s0 + r, y = s - k;
+                const int xs = (y < k) ? y : k;
+                if (y >= 0 && y < N && xs >= x0 && xs < x0 + TX) {
+                    const real Jv = Jj[r * TX + (xs - x0)];
+                    const V m = as[(s - j + APAD) * RS + c];
+                    const V y = as[(s - k + APAD) * RS + c];
+                    const V t = cmulc(m, y);
+                    caxpy(p.B, Jv, t);
+                }
+            }
+        }
+    }
+}
+
+template <typename real, int RS>
+__device__ __forceinline__ void process_block_dispatch(int mode, const typename vec2<real>::type *as, int c,
+                                                       int s0, int x0, int j, int k, int N, const real *Jj,
+                                                       const real *Jk, Partials<real> &p) {
+    if (mode == 3) process_block<real, RS, 3>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 1) process_block<real, RS, 1>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 2) process_block<real, RS, 2>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+}
+
+// Block ranges of an update: union of the runs of j and k in the sample's block list.
+struct Ranges {
+    int jlo, jhi, klo, khi, ulo, uhi;  // sample-local block indices [lo, hi)
+    int64_t jg, kg;                    // global block index of the first block of j's / k's run
+};
+__device__ __forceinline__ Ranges update_ranges(const SampleDev &sd, const int *bo, const int *mode_blk, int j,
+                                                int k) {
+    Ranges R;
+    const int stlo_j = j / TS, sthi_j = min((j + sd.N - 1) / TS, sd.ST - 1);
+    const int stlo_k = k / TS, sthi_k = min((k + sd.N - 1) / TS, sd.ST - 1);
+    R.jlo = bo[stlo_j]; R.jhi = bo[sthi_j + 1];
+    R.klo = bo[stlo_k]; R.khi = bo[sthi_k + 1];
+    R.ulo = min(R.jlo, R.klo); R.uhi = max(R.jhi, R.khi);
+    R.jg = sd.J_off + mode_blk[j];
+    R.kg = sd.J_off + mode_blk[k];
+    return R;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Proposal of a pair move and Metropolis test (Sec. III.A.1, readings R3 and R6).
+template <typename real> struct Proposal {
+    typename vec2<real>::type aj, ak, nj, nk;  // old and proposed amplitudes
+    real U;
+};
+
+template <typename real>
+__device__ __forceinline__ Proposal<real> make_proposal(uint64_t seed, uint32_t chain_id, uint32_t sweep,
+                                                        uint32_t update, typename vec2<real>::type aj,
+                                                        typename vec2<real>::type ak);
+
+template <>
+__device__ __forceinline__ Proposal<float> make_proposal<float>(uint64_t seed, uint32_t chain_id, uint32_t sweep,
+                                                                uint32_t update, float2 aj, float2 ak) {
+    Proposal<float> P;
+    P.aj = aj; P.ak = ak;
+    const u32x4 w = draw(seed, chain_id, sweep, update, kTagPropose);
+    const float uj = aj.x * aj.x + aj.y * aj.y, uk = ak.x * ak.x + ak.y * ak.y;
+    const float K = sqrtf(sqrtf(uj * uj + uk * uk));
+    const float kInv = 2.3283064365386963e-10f;
+    const float fj = ((float)w.x + 0.5f) * kInv, fk = ((float)w.y + 0.5f) * kInv, ft = ((float)w.z + 0.5f) * kInv;
+    float sj, cj, sk, ck, st, ct;
+    sincospif(2.0f * fj, &sj, &cj);
+    sincospif(2.0f * fk, &sk, &ck);
+    sincospif(0.5f * ft, &st, &ct);
+    const float Aj = K * sqrtf(ct), Ak = K * sqrtf(st);
+    P.nj = make_float2(Aj * cj, Aj * sj);
+    P.nk = make_float2(Ak * ck, Ak * sk);
+    P.U = ((float)w.w + 0.5f) * kInv;
+    return P;
+}
+
+template <>
+__device__ __forceinline__ Proposal<double> make_proposal<double>(uint64_t seed, uint32_t chain_id,
+                                                                  uint32_t sweep, uint32_t update, double2 aj,
+                                                                  double2 ak) {
+    Proposal<double> P;
+    P.aj = aj; P.ak = ak;
+    const u32x4 w = draw(seed, chain_id, sweep, update, kTagPropose);
+    const double uj = aj.x * aj.x + aj.y * aj.y, uk = ak.x * ak.x + ak.y * ak.y;
+    const double K = sqrt(sqrt(uj * uj + uk * uk));
+    const double phj = kTwoPi * u01(w.x), phk = kTwoPi * u01(w.y), th = kHalfPi * u01(w.z);
+    const double Aj = K * sqrt(cos(th)), Ak = K * sqrt(sin(th));
+    double sj, cj, sk, ck;
+    sincos(phj, &sj, &cj);
+    sincos(phk, &sk, &ck);
+    P.nj = make_double2(Aj * cj, Aj * sj);
+    P.nk = make_double2(Ak * ck, Ak * sk);
+    P.U = u01(w.w);
+    return P;
+}
+
+template <typename real>
+__device__ __forceinline__ real delta_h(const Proposal<real> &P, const Partials<real> &f, real cc) {
+    using V = typename vec2<real>::type;
+    V dj, dk;
+    dj.x = P.nj.x - P.aj.x; dj.y = P.nj.y - P.aj.y;
+    dk.x = P.nk.x - P.ak.x; dk.y = P.nk.y - P.ak.y;
+    const V t1 = cmulc(dj, f.hj), t2 = cmulc(dk, f.hk);
+    const V djdk = cmulc(dj, dk);  // conj(dj) dk
+    V cdjcdk;                      // conj(dj) conj(dk)
+    cdjcdk.x = dj.x * dk.x - dj.y * dk.y;
+    cdjcdk.y = -(dj.x * dk.y + dj.y * dk.x);
+    const V t3 = cmul(djdk, f.B), t4 = cmul(cdjcdk, f.A);
+    return -cc * (t1.x + t2.x + t3.x + t4.x);
+}
+
+__device__ __forceinline__ bool metropolis_accept(float dH, float beta, float U) {
+    return dH <= 0.0f || U < expf(-beta * dH);
+}
+__device__ __forceinline__ bool metropolis_accept(double dH, double beta, double U) {
+    return dH <= 0.0 || U < exp(-beta * dH);
+}
+
+// ------------------------------------------------------------------------------------------------
+// The persistent sweep kernel.  NCW consumer warps + 1 producer warp.  A consumer lane is
+// (chain c = lane % G, worker q = lane / G); worker w = warp * (32/G) + q takes block w of every
+// chunk of CB = NCW*32/G blocks.  The producer warp streams the J runs of j and k, chunk by chunk,
+// into an NST-stage ring.  Work units = (group, run of sweeps) come from a ticket counter; a unit
+// waits (bounded) until the previous run of its group has been written back.
+template <typename real, int G, int NCW> struct SweepShape {
+    static constexpr int WPW = 32 / G;
+    static constexpr int NW = NCW * WPW;
+    static constexpr int CB = NW;
+    static constexpr int NST = 3;
+    static constexpr int RS = RowStride<real, G>::value;
+    static constexpr int NTHREADS = (NCW + 1) * 32;
+    static constexpr size_t stage_bytes = (size_t)2 * CB * TBLK * sizeof(real);
+};
+
+template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
+    using Sh = SweepShape<real, G, NCW>;
+    using V = typename vec2<real>::type;
+    size_t b = 0;
+    b += 2 * Sh::NST * sizeof(uint64_t);                                  // mbarriers
+    b = (b + 127) / 128 * 128;
+    b += Sh::NST * Sh::stage_bytes;                                       // J ring
+    b += (size_t)(maxN + 2 * APAD) * Sh::RS * sizeof(V);                  // amplitudes
+    b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
+    b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
+    b += (size_t)(2 * 128 + 8) * sizeof(int);                             // bo / xtlo tables
+    b += 64;
+    return b;
+}
+
+template <typename real, int G, int NCW>
+__global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams prm) {
+    using Sh = SweepShape<real, G, NCW>;
+    using V = typename vec2<real>::type;
+    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW;
+    constexpr int NCT = NCW * 32;  // consumer threads
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + NST;
+    size_t off = (2 * NST * sizeof(uint64_t) + 127) / 128 * 128;
+    real *ring = reinterpret_cast<real *>(smem + off);
+    off += NST * Sh::stage_bytes;
+    V *as = reinterpret_cast<V *>(smem + off);
+    off += (size_t)(prm.maxN + 2 * APAD) * RS * sizeof(V);
+    real *red = reinterpret_cast<real *>(smem + off);
+    off += (size_t)2 * NCW * G * 8 * sizeof(real);
+    double *cE = reinterpret_cast<double *>(smem + off);
+    off += G * sizeof(double);
+    real *cBeta = reinterpret_cast<real *>(smem + off);
+    off += G * sizeof(real);
+    uint32_t *cId = reinterpret_cast<uint32_t *>(smem + off);
+    off += G * sizeof(uint32_t);
+    uint32_t *cAcc = reinterpret_cast<uint32_t *>(smem + off);
+    off += G * sizeof(uint32_t);
+    off = (off + 7) / 8 * 8;
+    unsigned long long *cAtt = reinterpret_cast<unsigned long long *>(smem + off);
+    off += G * sizeof(unsigned long long);
+    int *s_bo = reinterpret_cast<int *>(smem + off);
+    off += 129 * sizeof(int);
+    int *s_xtlo = reinterpret_cast<int *>(smem + off);
+    off += 129 * sizeof(int);
+    int *s_unit = reinterpret_cast<int *>(smem + off);  // [0] group, [1] chunk, [2] abort
+    volatile int *abort_flag = s_unit + 2;
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const bool producer = (warp == NCW);
+    const int c = lane % G, wq = lane / G;
+    const int worker = warp * WPW + wq;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NCW);
+        }
+        s_unit[2] = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+
+    const long long sweep_base = prm.ctl->sweep_base;
+    const int n_sweeps = prm.n_sweeps, spu = prm.sweeps_per_unit;
+    const int chunks_per_group = (n_sweeps + spu - 1) / spu;
+    const unsigned total_units = (unsigned)chunks_per_group * (unsigned)prm.n_groups;
+    const real *J = reinterpret_cast<const real *>(prm.J);
+    V *A = reinterpret_cast<V *>(prm.a);
+    uint32_t q = 0;  // global chunk counter (ring position)
+    int red_par = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            int g = -1, ci = 0;
+            if (!*abort_flag) {
+                const unsigned t = atomicAdd(&prm.ctl->ticket, 1u);
+                if (t < total_units) {
+                    g = (int)(t % (unsigned)prm.n_groups);
+                    ci = (int)(t / (unsigned)prm.n_groups);
+                    // wait until the previous run of this group is written back
+                    const unsigned long long t0 = global_ns();
+                    while (true) {
+                        int v;
+                        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(prm.progress + g) : "memory");
+                        if (v >= ci) break;
+                        if (global_ns() - t0 > kWaitNs) { record_error(prm.ctl, kErrTimeout, 1); *abort_flag = 1; g = -1; break; }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            s_unit[0] = g; s_unit[1] = ci;
+        }
+        __syncthreads();
+        const int g = s_unit[0], ci = s_unit[1];
+        if (g < 0) break;
+        const GroupDev gr = prm.groups[g];
+        const SampleDev sd = prm.samples[gr.sample];
+        const int N = sd.N;
+        const int sw0 = ci * spu, sw1 = min(n_sweeps, sw0 + spu);
+
+        // ---- unit set-up: tables, chain metadata, amplitudes (consumers); producer starts streaming
+        if (!producer) {
+            for (int i = tid; i <= sd.ST; i += NCT) s_bo[i] = prm.bo[sd.tab_off + i];
+            for (int i = tid; i < sd.ST; i += NCT) s_xtlo[i] = prm.xtlo[sd.tab_off + i];
+            if (tid < G) {
+                const int slot = gr.chain0 + tid;
+                if (tid < gr.count) {
+                    const int t = prm.label[slot];
+                    const int r = (slot - sd.chain0) / prm.nT;
+                    cE[tid] = __ldcg(prm.E + slot);
+                    cBeta[tid] = (real)prm.beta[t];
+                    cId[tid] = (uint32_t)((gr.sample * prm.R + r) * prm.nT + t);
+                } else {
+                    cE[tid] = 0.0; cBeta[tid] = real(0); cId[tid] = 0u;
+                }
+                cAcc[tid] = 0u; cAtt[tid] = 0ull;
+            }
+            const int rows = N + 2 * APAD;
+            for (int i = tid; i < rows * G; i += NCT) {
+                const int x = i / G - APAD, cc = i % G;
+                V v; v.x = v.y = real(0);
+                if (x >= 0 && x < N && cc < gr.count) {
+                    const V *src = A + sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N + x;
+                    if (sizeof(real) == 4) {
+                        const float2 t = __ldcg(reinterpret_cast<const float2 *>(src));
+                        v.x = (real)t.x; v.y = (real)t.y;
+                    } else {
+                        const double2 t = __ldcg(reinterpret_cast<const double2 *>(src));
+                        v.x = (real)t.x; v.y = (real)t.y;
+                    }
+                }
+                as[(x + APAD) * RS + cc] = v;
+            }
+            named_bar(1, NCT);
+        }
+
+        if (producer) {
+            // ---------------- producer warp: stream J runs of (j,k) for every update of the unit
+            const int *bo_g = prm.bo + sd.tab_off;
+            bool stop = false;
+            for (int sw = sw0; sw < sw1 && !stop; ++sw) {
+                const uint32_t sweep = (uint32_t)(sweep_base + sw);
+                for (int u = 0; u < N / 2 && !stop; ++u) {
+                    stop = __shfl_sync(0xffffffffu, *abort_flag, 0) != 0;  // warp-uniform
+                    if (stop) break;
+                    int j, k;
+                    pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
+                    const Ranges Rg = update_ranges(sd, bo_g, prm.mode_blk + sd.mode_off, j, k);
+                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q) {
+                        const int stage = q % NST;
+                        const uint32_t ph = (q / NST) & 1u;
+                        if (lane == 0) {
+                            const bool ok = mbar_wait_bounded(&empty[stage], ph ^ 1u, prm.ctl, 2, abort_flag);
+                            const int ce = min(cb + CB, Rg.uhi);
+                            const int a0 = max(cb, Rg.jlo), a1 = min(ce, Rg.jhi);
+                            const int b0 = max(cb, Rg.klo), b1 = min(ce, Rg.khi);
+                            const uint32_t bj = a1 > a0 ? (uint32_t)(a1 - a0) * TBLK * sizeof(real) : 0u;
+                            const uint32_t bk = b1 > b0 ? (uint32_t)(b1 - b0) * TBLK * sizeof(real) : 0u;
+                            real *st_j = ring + (size_t)stage * 2 * CB * TBLK;
+                            real *st_k = st_j + (size_t)CB * TBLK;
+                            if (ok) mbar_arrive_expect_tx(&full[stage], bj + bk);
+                            if (ok && bj) bulk_g2s(st_j + (size_t)(a0 - cb) * TBLK, J + (Rg.jg + (a0 - Rg.jlo)) * TBLK, bj, &full[stage]);
+                            if (ok && bk) bulk_g2s(st_k + (size_t)(b0 - cb) * TBLK, J + (Rg.kg + (b0 - Rg.klo)) * TBLK, bk, &full[stage]);
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        } else {
+            // ---------------- consumer warps
+            const int *mode_blk = prm.mode_blk + sd.mode_off;
+            const uint32_t *binfo = prm.blkinfo + sd.blk_off;
+            const real cc = (real)prm.cc;
+            for (int sw = sw0; sw < sw1; ++sw) {
+                const uint32_t sweep = (uint32_t)(sweep_base + sw);
+                for (int u = 0; u < N / 2; ++u) {
+                    int j, k;
+                    pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
+                    const Ranges Rg = update_ranges(sd, s_bo, mode_blk, j, k);
+                    // proposal for chain c (lanes of worker 0 of every warp, redundantly)
+                    Proposal<real> P;
+                    if (wq == 0) {
+                        const V aj = as[(j + APAD) * RS + c], ak = as[(k + APAD) * RS + c];
+                        P = make_proposal<real>(prm.seed, cId[c], sweep, (uint32_t)u, aj, ak);
+                    }
+                    Partials<real> pr;
+                    pr.zero();
+                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q) {
+                        const int stage = q % NST;
+                        const uint32_t ph = (q / NST) & 1u;
+                        mbar_wait_bounded(&full[stage], ph, prm.ctl, 3, abort_flag);
+                        const int b = cb + worker;
+                        if (b < Rg.uhi && !*abort_flag) {
+                            const uint32_t info = __ldg(binfo + b);
+                            const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
+                            const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
+                            const real *st_j = ring + (size_t)stage * 2 * CB * TBLK + (size_t)worker * TBLK;
+                            const real *st_k = st_j + (size_t)CB * TBLK;
+                            process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[stage]);
+                    }
+                    // reduce over the workers of this warp, then across warps through shared memory
+                    real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
+#pragma unroll
+                    for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+                    real *rb = red + (size_t)red_par * NCW * G * 8;
+                    if (wq == 0) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) rb[(warp * G + c) * 8 + e] = v[e];
+                    }
+                    named_bar(1, NCT);
+                    if (wq == 0) {
+                        Partials<real> f;
+                        f.zero();
+                        real t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        for (int w = 0; w < NCW; ++w)
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) t[e] += rb[(w * G + c) * 8 + e];
+                        f.hj.x = t[0]; f.hj.y = t[1]; f.hk.x = t[2]; f.hk.y = t[3];
+                        f.B.x = t[4]; f.B.y = t[5]; f.A.x = t[6]; f.A.y = t[7];
+                        const real dH = delta_h<real>(P, f, cc);
+                        const bool acc = (c < gr.count) && metropolis_accept(dH, cBeta[c], P.U);
+                        if (acc) {
+                            as[(j + APAD) * RS + c] = P.nj;
+                            as[(k + APAD) * RS + c] = P.nk;
+                        }
+                        if (warp == 0 && c < gr.count) {
+                            if (acc) { cE[c] += (double)dH; cAcc[c] += 1u; }
+                            cAtt[c] += 1ull;
+                        }
+                    }
+                    red_par ^= 1;
+                    __syncwarp();
+                }
+                // interior measurement point: snapshot amplitudes and energies
+                const long long done = sweep_base + sw + 1;
+                if (prm.measure_every > 0 && done % prm.measure_every == 0 && sw + 1 < n_sweeps) {
+                    named_bar(1, NCT);
+                    // snapshot index = number of measurement points in (sweep_base, done], minus one
+                    const int kk = (int)(done / prm.measure_every - sweep_base / prm.measure_every - 1);
+                    if (kk >= 0 && kk < prm.n_snap_max) {
+                        V *dst = reinterpret_cast<V *>(prm.snap_a) + (int64_t)kk * prm.a_total + sd.a_off +
+                                 (int64_t)(gr.chain0 - sd.chain0) * N;
+                        for (int i = tid; i < N * gr.count; i += NCT) {
+                            const int cc2 = i / N, x = i % N;
+                            dst[(int64_t)cc2 * N + x] = as[(x + APAD) * RS + cc2];
+                        }
+                        if (tid < gr.count) prm.snap_E[(int64_t)kk * prm.n_chains + gr.chain0 + tid] = cE[tid];
+                    }
+                    named_bar(1, NCT);
+                }
+            }
+            // ---- write back the group's state and counters
+            named_bar(1, NCT);
+            for (int i = tid; i < N * gr.count; i += NCT) {
+                const int cc2 = i / N, x = i % N;
+                V *dst = A + sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc2) * N + x;
+                __stcg(dst, as[(x + APAD) * RS + cc2]);
+            }
+            if (tid < gr.count) {
+                const int slot = gr.chain0 + tid;
+                __stcg(prm.E + slot, cE[tid]);
+                prm.mc_acc[slot] += cAcc[tid];
+                prm.mc_att[slot] += cAtt[tid];
+            }
+            __threadfence();
+            named_bar(1, NCT);
+            if (tid == 0) {
+                asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(prm.progress + g), "r"(ci + 1) : "memory");
+            }
+        }
+    }
+    // never leave bulk copies in flight behind an exiting block (only possible after an abort)
+    if (producer && lane == 0) {
+        const uint32_t first = q > (uint32_t)NST ? q - NST : 0u;
+        for (uint32_t qq = first; qq < q; ++qq) {
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&full[qq % NST], (qq / NST) & 1u) && global_ns() - t0 < kWaitNs) {
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Field-only kernel: the same block arithmetic with J read straight from global memory; one thread
+// block per group of the chosen sample.  Output: 8 doubles per chain (h_j, h_k, B_jk, A_jk).
+template <typename real, int G>
+__global__ void fields_kernel(FieldsParams prm) {
+    using V = typename vec2<real>::type;
+    constexpr int RS = RowStride<real, G>::value, NCW = 4, WPW = 32 / G, NW = NCW * WPW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    V *as = reinterpret_cast<V *>(smem);
+    const GroupDev gr = prm.groups[prm.group0 + blockIdx.x];
+    const SampleDev sd = prm.samples[gr.sample];
+    const int N = sd.N, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int c = lane % G, worker = warp * WPW + lane / G;
+    const V *A = reinterpret_cast<const V *>(prm.a);
+    real *red = reinterpret_cast<real *>(smem + (size_t)(N + 2 * APAD) * RS * sizeof(V));
+    for (int i = tid; i < (N + 2 * APAD) * G; i += blockDim.x) {
+        const int x = i / G - APAD, cc = i % G;
+        V v; v.x = v.y = real(0);
+        if (x >= 0 && x < N && cc < gr.count) v = A[sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N + x];
+        as[(x + APAD) * RS + cc] = v;
+    }
+    __syncthreads();
+    const int j = prm.j, k = prm.k;
+    const Ranges Rg = update_ranges(sd, prm.bo + sd.tab_off, prm.mode_blk + sd.mode_off, j, k);
+    const real *J = reinterpret_cast<const real *>(prm.J);
+    Partials<real> pr;
+    pr.zero();
+    for (int b = Rg.ulo + worker; b < Rg.uhi; b += NW) {
+        const uint32_t info = prm.blkinfo[sd.blk_off + b];
+        const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
+        const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
+        const real *Jj = J + (Rg.jg + (b - Rg.jlo)) * TBLK;
+        const real *Jk = J + (Rg.kg + (b - Rg.klo)) * TBLK;
+        process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, Jj, Jk, pr);
+    }
+    real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+    if (lane < G)
+        for (int e = 0; e < 8; ++e) red[(warp * G + c) * 8 + e] = v[e];
+    __syncthreads();
+    if (tid < G * 8 && tid / 8 < gr.count) {
+        const int cc = tid / 8, e = tid % 8;
+        double t = 0.0;
+        for (int w = 0; w < NCW; ++w) t += (double)red[(w * G + cc) * 8 + e];
+        prm.out[(int64_t)(gr.chain0 - sd.chain0 + cc) * 8 + e] = t;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Full energy (resync).  With the half fields h^+_x = sum_{m > x} conj(a_m) acc_x[x+m],
+//     H = -(cc/2) sum_x Re( conj(a_x) h^+_x ),
+// which visits every quadruplet twice (once per pair).  Products and row sums in `real`, per-block
+// sums accumulated in FP64.  With renorm != 0 the chain is first rescaled onto sum |a|^4 = N.
+template <typename real, int G>
+__global__ void energy_kernel(EnergyParams prm) {
+    using V = typename vec2<real>::type;
+    constexpr int RS = RowStride<real, G>::value, NCW = 8, WPW = 32 / G, NW = NCW * WPW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const GroupDev gr = prm.groups[blockIdx.x];
+    const SampleDev sd = prm.samples[gr.sample];
+    const int N = sd.N, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int c = lane % G, worker = warp * WPW + lane / G;
+    V *as = reinterpret_cast<V *>(smem);
+    double *dred = reinterpret_cast<double *>(smem + (size_t)(N + 2 * APAD) * RS * sizeof(V));
+    __shared__ double s_f[32];
+    V *Ag = reinterpret_cast<V *>(prm.a);
+    for (int i = tid; i < (N + 2 * APAD) * G; i += blockDim.x) {
+        const int x = i / G - APAD, cc = i % G;
+        V v; v.x = v.y = real(0);
+        if (x >= 0 && x < N && cc < gr.count) v = Ag[sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N + x];
+        as[(x + APAD) * RS + cc] = v;
+    }
+    __syncthreads();
+    if (prm.renorm) {
+        // sum |a|^4 per chain in FP64 (one warp per chain, round robin)
+        for (int cc = warp; cc < gr.count; cc += NCW) {
+            double s4 = 0.0;
+            for (int x = lane; x < N; x += 32) {
+                const V v = as[(x + APAD) * RS + cc];
+                const double u = (double)v.x * v.x + (double)v.y * v.y;
+                s4 += u * u;
+            }
+            for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            if (lane == 0) {
+                if (!(s4 > 0.0) || !isfinite(s4)) record_error(prm.ctl, kErrNaN, 10);
+                s_f[cc] = sqrt(sqrt((double)N / s4));
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < N * gr.count; i += blockDim.x) {
+            const int cc = i / N, x = i % N;
+            V v = as[(x + APAD) * RS + cc];
+            const double f = s_f[cc];
+            v.x = (real)((double)v.x * f); v.y = (real)((double)v.y * f);
+            as[(x + APAD) * RS + cc] = v;
+            Ag[sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N + x] = v;
+        }
+        __syncthreads();
+    }
+    const real *J = reinterpret_cast<const real *>(prm.J);
+    const int *bo = prm.bo + sd.tab_off;
+    const int *mode_blk = prm.mode_blk + sd.mode_off;
+    const int *ebo = prm.ebo + sd.mode_off;  // prefix over x of the blocks with rows s > 2x
+    const int total = ebo[N];
+    double e = 0.0;
+    int x = 0;
+    for (int it = worker; it < total; it += NW) {
+        while (ebo[x + 1] <= it) ++x;
+        const int stlo = x / TS;
+        const int sta = (2 * x + 1) / TS;
+        const int b = bo[sta] + (it - ebo[x]);
+        const uint32_t info = prm.blkinfo[sd.blk_off + b];
+        const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
+        const real *Jx = J + (sd.J_off + mode_blk[x] + (b - bo[stlo])) * TBLK;
+        const int s0 = st * TS, x0 = xt * TX;
+        V ax[TX], ay[TS + TX - 1];
+#pragma unroll
+        for (int i = 0; i < TX; ++i) ax[i] = as[(x0 + i + APAD) * RS + c];
+        const int ybase = s0 - x0 - (TX - 1) + APAD;
+#pragma unroll
+        for (int d = 0; d < TS + TX - 1; ++d) ay[d] = as[(ybase + d) * RS + c];
+        const V axx = as[(x + APAD) * RS + c];
+        real blk = real(0);
+#pragma unroll
+        for (int r = 0; r < TS; ++r) {
+            const int s = s0 + r, m = s - x;
+            if (m > x && m < N) {
+                JRow<real> jr;
+                jr.load(Jx + r * TX);
+                V acc; acc.x = acc.y = real(0);
+#pragma unroll
+                for (int i = 0; i < TX; ++i) caxpy(acc, jr.v[i], cmul(ax[i], ay[r - i + TX - 1]));
+                const V am = as[(m + APAD) * RS + c];
+                const V zz = cmul(axx, am);          // z_{x,m}
+                blk += zz.x * acc.x + zz.y * acc.y;  // Re(conj(z) acc)
+            }
+        }
+        e += (double)blk;
+    }
+    for (int o = G; o < 32; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane < G) dred[warp * G + c] = e;
+    __syncthreads();
+    if (tid < gr.count) {
+        double t = 0.0;
+        for (int w = 0; w < NCW; ++w) t += dred[w * G + tid];
+        const double E = -0.5 * prm.cc * t;
+        if (!isfinite(E)) record_error(prm.ctl, kErrNaN, 11);
+        if (prm.E_out) prm.E_out[gr.chain0 + tid] = E;
+        if (prm.E_state) prm.E_state[gr.chain0 + tid] = E;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host launchers
+template <typename real, int G, int NCW>
+static cudaError_t launch_sweep_t(const SweepParams &p, int grid, cudaStream_t s) {
+    const size_t sm = sweep_smem_bytes<real, G, NCW>(p.maxN);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<real, G, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<real, G, NCW><<<grid, (NCW + 1) * 32, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename real, int G, int NCW>
+static int occupancy_t(int maxN) {
+    const size_t sm = sweep_smem_bytes<real, G, NCW>(maxN);
+    if (cudaFuncSetAttribute(sweep_kernel<real, G, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<real, G, NCW>, (NCW + 1) * 32, sm) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+#define PT_SWEEP_VARIANTS(X)            \
+    X(float, 8, 8) X(float, 8, 16)      \
+    X(float, 16, 8) X(float, 16, 16)    \
+    X(float, 32, 4) X(float, 32, 8)     \
+    X(double, 8, 8) X(double, 16, 4)
+
+bool sweep_variant_exists(bool dbl, int G, int ncw) {
+#define X(T, g, n) if (dbl == (sizeof(T) == 8) && G == g && ncw == n) return true;
+    PT_SWEEP_VARIANTS(X)
+#undef X
+    return false;
+}
+
+cudaError_t launch_sweep(bool dbl, int G, int ncw, const SweepParams &p, int grid, cudaStream_t s) {
+#define X(T, g, n) \
+    if (dbl == (sizeof(T) == 8) && G == g && ncw == n) return launch_sweep_t<T, g, n>(p, grid, s);
+    PT_SWEEP_VARIANTS(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+int sweep_occupancy(bool dbl, int G, int ncw, int maxN) {
+#define X(T, g, n) \
+    if (dbl == (sizeof(T) == 8) && G == g && ncw == n) return occupancy_t<T, g, n>(maxN);
+    PT_SWEEP_VARIANTS(X)
+#undef X
+    return 0;
+}
+
+template <typename real, int G>
+static cudaError_t launch_fields_t(const FieldsParams &p, int ngroups, int maxN, cudaStream_t s) {
+    using V = typename vec2<real>::type;
+    const size_t sm = (size_t)(maxN + 2 * APAD) * RowStride<real, G>::value * sizeof(V) + 4 * G * 8 * sizeof(real) + 64;
+    cudaError_t e = cudaFuncSetAttribute(fields_kernel<real, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fields_kernel<real, G><<<ngroups, 128, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(bool dbl, int G, const FieldsParams &p, int ngroups, int maxN, cudaStream_t s) {
+    if (!dbl) {
+        if (G == 8) return launch_fields_t<float, 8>(p, ngroups, maxN, s);
+        if (G == 16) return launch_fields_t<float, 16>(p, ngroups, maxN, s);
+        if (G == 32) return launch_fields_t<float, 32>(p, ngroups, maxN, s);
+    } else {
+        if (G == 8) return launch_fields_t<double, 8>(p, ngroups, maxN, s);
+        if (G == 16) return launch_fields_t<double, 16>(p, ngroups, maxN, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename real, int G>
+static cudaError_t launch_energy_t(const EnergyParams &p, int ngroups, int maxN, cudaStream_t s) {
+    using V = typename vec2<real>::type;
+    const size_t sm = (size_t)(maxN + 2 * APAD) * RowStride<real, G>::value * sizeof(V) + 8 * G * sizeof(double) + 64;
+    cudaError_t e = cudaFuncSetAttribute(energy_kernel<real, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    energy_kernel<real, G><<<ngroups, 256, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(bool dbl, int G, const EnergyParams &p, int ngroups, int maxN, cudaStream_t s) {
+    if (!dbl) {
+        if (G == 8) return launch_energy_t<float, 8>(p, ngroups, maxN, s);
+        if (G == 16) return launch_energy_t<float, 16>(p, ngroups, maxN, s);
+        if (G == 32) return launch_energy_t<float, 32>(p, ngroups, maxN, s);
+    } else {
+        if (G == 8) return launch_energy_t<double, 8>(p, ngroups, maxN, s);
+        if (G == 16) return launch_energy_t<double, 16>(p, ngroups, maxN, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ptgb
