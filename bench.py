@@ -230,6 +230,25 @@ def run_gpu(args, rank, world, dist):
                 e2e=e2e, fl=fl)
 
 
+def profile_case():
+    """Three launches of the sweep kernel (one sweep each) on half the bench workload: 8 samples
+    (176 MB of couplings, larger than L2), 768 chains; no measurement, resync or swap."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    pkg.build()
+    W = workload.workloads()["n256_large"]
+    nq = len(pkg.enumerate_quads(N_MODES))
+    Js = [workload.couplings(N_MODES, nq, s) for s in W.seeds[:8]]
+    pt = pkg.PT(W.Ns[:8], Js, W.temps, W.replicas, 5, precision="fp32", swap_every=0, measure_every=0,
+                resync_every=0, use_graphs=False)
+    for _ in range(3):
+        pt.sweep(1)
+    pt.sync()
+    print("profile case done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,7 +256,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
