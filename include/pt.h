@@ -174,6 +174,30 @@ int pt_destroy(pt_ctx *ctx);
 /* Message of the last failing call on ctx (or of the last failing pt_create when ctx is NULL). */
 const char *pt_last_error(const pt_ctx *ctx);
 
+/* Allocation-free FP64 energies of a batch of chains.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory (a program whose device memory belongs to
+ * another runtime's pool, a real-time loop where cudaMalloc/cudaFree would synchronise the device, a
+ * plug-in limited to the buffers its host hands it).  It computes the same H as pt_energy of a
+ * PT_PREC_FP64_PLAIN context, one thread block per chain.
+ *  N         modes, 4 <= N <= 64 (PT_EINVAL otherwise: the working table has room for the 20336
+ *            quadruplets of the 64-mode comb).
+ *  n_chains  chains (0 returns PT_OK at once).
+ *  J         device pointer: the N-mode couplings in canonical quadruplet order (pt_enumerate_quads).
+ *  a         device pointer: n_chains * N complex amplitudes, interleaved (re, im) doubles, chain-major.
+ *  E         device pointer: n_chains doubles receive H of each chain.
+ *  cc        multiplier of the quadruplet sum (2 for the paper's "+ c.c.").
+ *  stream    cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
+ * Caller owns J, a and E.  The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine): its working table is a static device array of 20336 int4 (325 KB) that every GPU loading
+ * the library holds until exit.  Every call rewrites the part of the table it uses, so a call never
+ * sees stale contents, but all calls share the one table: calls that overlap on the GPU (other streams
+ * or threads, same device) race and must be serialised by the caller.  The first call on a device
+ * looks up the table's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Errors: PT_EINVAL (arguments), PT_ECUDA (no device, lookup or
+ * launch failure); the message is in pt_last_error(NULL). */
+int pt_energy_fp64_static(int N, int n_chains, const double *J, const double *a, double *E, double cc,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

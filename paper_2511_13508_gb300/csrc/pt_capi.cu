@@ -20,8 +20,14 @@
 using namespace ptgb;
 
 namespace {
-
 thread_local std::string g_create_error;
+}
+
+namespace ptgb {
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace ptgb
+
+namespace {
 
 // Counts the quadruplets of the N-mode comb: for every (a,b) with a<b the admissible c run over
 // b+1 .. N-1-(b-a) (then d = b+c-a lies in (c, N)).
