@@ -304,7 +304,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
                              "frac": r["achieved"] / r["peak"], "traffic": None,
-                             "kernel": "sweep_kernel<float,8,16>", "kernel_ms_per_launch": r["kms"],
+                             "kernel": "sweep_kernel<float,8,15> (8 chains x 15 field warps + 1 copy warp per block)", "kernel_ms_per_launch": r["kms"],
                              "flops_per_launch": r["fl"],
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)"},
                 "cpu_baseline": cpu,

@@ -69,6 +69,7 @@ typedef struct pt_config {
     int chains_per_block; /* chains sharing one J stream inside a thread block: 0 = tuned, or 8/16/32 */
     int sweeps_per_unit;  /* sweeps in one scheduling unit of the persistent kernel; 0 = tuned */
     int blocks_per_sm;    /* persistent thread blocks per SM; 0 = tuned */
+    int consumer_warps;   /* field-computing warps per thread block (plus one copy warp); 0 = tuned */
     int use_graphs;       /* replay each sweep segment as a captured CUDA graph (default 1) */
     int watchdog_ms;      /* host watchdog on synchronising calls; 0 = wait forever (default 600000) */
 } pt_config;

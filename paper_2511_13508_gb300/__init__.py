@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cc_factor", ctypes.c_double), ("swap_every", ctypes.c_int),
                 ("measure_every", ctypes.c_int), ("resync_every", ctypes.c_int),
                 ("chains_per_block", ctypes.c_int), ("sweeps_per_unit", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("use_graphs", ctypes.c_int), ("watchdog_ms", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("consumer_warps", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("watchdog_ms", ctypes.c_int)]
 
 
 class Observables(ctypes.Structure):
@@ -125,7 +126,7 @@ class PT:
 
     def __init__(self, Ns, J_list, temps, replicas, seed, precision="fp32", cc=2.0, swap_every=64,
                  measure_every=16, resync_every=64, chains_per_block=0, sweeps_per_unit=0, blocks_per_sm=0,
-                 use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True):
+                 consumer_warps=0, use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True):
         L = lib()
         self.Ns = np.ascontiguousarray(Ns, dtype=np.int32)
         self.S, self.R = len(self.Ns), int(replicas)
@@ -140,7 +141,7 @@ class PT:
         cfg.precision = PREC[precision]; cfg.cc_factor = cc; cfg.swap_every = swap_every
         cfg.measure_every = measure_every; cfg.resync_every = resync_every
         cfg.chains_per_block = chains_per_block; cfg.sweeps_per_unit = sweeps_per_unit
-        cfg.blocks_per_sm = blocks_per_sm; cfg.use_graphs = int(bool(use_graphs)); cfg.watchdog_ms = watchdog_ms
+        cfg.blocks_per_sm = blocks_per_sm; cfg.consumer_warps = consumer_warps; cfg.use_graphs = int(bool(use_graphs)); cfg.watchdog_ms = watchdog_ms
         self._alloc = None
         s_ptr = None
         if stream is not None:

@@ -93,7 +93,8 @@ SampleLayout make_layout(int N) {
 
 // Fills the blocked store of one sample: for mode l and block (st, xt) of its run, entry (r, i) is
 // J of the quadruplet {l, m = s-l, x, s-x} with s = st*TS+r, x = xt*TX+i, or 0 when that is not a
-// quadruplet of distinct modes.
+// quadruplet of distinct modes.  Blocks are column-major (entry (r, i) at i*TS + r) and padded to
+// JStride reals.
 template <typename real>
 void pack_sample(const SampleLayout &L, const double *J, real *dst) {
     const int N = L.N;
@@ -104,7 +105,8 @@ void pack_sample(const SampleLayout &L, const double *J, real *dst) {
         int64_t bpos = L.mode_blk[l];
         for (int b = L.bo[stlo]; b < L.bo[sthi + 1]; ++b, ++bpos) {
             const int st = (int)(L.blkinfo[b] >> 16), xt = (int)(L.blkinfo[b] & 0xffffu);
-            real *blk = dst + bpos * TBLK;
+            real *blk = dst + bpos * JStride<real>::value;
+            for (int e = TBLK; e < JStride<real>::value; ++e) blk[e] = real(0);
             for (int r = 0; r < TS; ++r)
                 for (int i = 0; i < TX; ++i) {
                     const int s = st * TS + r, x = xt * TX + i, m = s - l, y = s - x;
@@ -116,7 +118,7 @@ void pack_sample(const SampleLayout &L, const double *J, real *dst) {
                         const int64_t idx = off[(size_t)q[0] * N + q[1]] + (q[2] - q[1] - 1);
                         v = (real)J[idx];
                     }
-                    blk[r * TX + i] = v;
+                    blk[i * TS + r] = v;
                 }
         }
     }
@@ -370,6 +372,7 @@ void pt_config_default(pt_config *cfg) {
     cfg->chains_per_block = 0;
     cfg->sweeps_per_unit = 0;
     cfg->blocks_per_sm = 0;
+    cfg->consumer_warps = 0;
     cfg->use_graphs = 1;
     cfg->watchdog_ms = 600000;
 }
@@ -465,8 +468,10 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
         else G = (c->maxN >= 128) ? 8 : (c->maxN >= 48 ? 16 : 32);
         if (G > 8 && chains_ps <= 8) G = 8;
     }
-    if (c->dbl) ncw = (G == 16) ? 4 : 8;
-    else ncw = (G == 8) ? 8 : (G == 16 ? 8 : 4);
+    // consumer warps: with the producer warp the block is a multiple of four warps
+    if (c->dbl) ncw = (G == 16) ? 3 : 7;
+    else ncw = (G == 8) ? (c->maxN >= 128 ? 15 : 7) : (G == 16 ? 7 : 3);
+    if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;
     c->spu = cfg.sweeps_per_unit > 0 ? cfg.sweeps_per_unit
@@ -549,12 +554,13 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
 
     // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
     if (!c->plain) {
-        c->d_J = dev_alloc(c, (size_t)jblocks * TBLK * c->esize);
+        const size_t js = c->dbl ? JStride<double>::value : JStride<float>::value;
+        c->d_J = dev_alloc(c, (size_t)jblocks * js * c->esize);
         if (!c->d_J) return bail(fail(c, PT_ENOMEM, "device allocation failed (couplings)"));
-        std::vector<unsigned char> hJ((size_t)jblocks * TBLK * c->esize);
+        std::vector<unsigned char> hJ((size_t)jblocks * js * c->esize);
         for (int s = 0; s < S; ++s) {
-            if (c->dbl) pack_sample<double>(lay[s], J + J_offsets[s], reinterpret_cast<double *>(hJ.data()) + c->samples[s].J_off * TBLK);
-            else pack_sample<float>(lay[s], J + J_offsets[s], reinterpret_cast<float *>(hJ.data()) + c->samples[s].J_off * TBLK);
+            if (c->dbl) pack_sample<double>(lay[s], J + J_offsets[s], reinterpret_cast<double *>(hJ.data()) + c->samples[s].J_off * js);
+            else pack_sample<float>(lay[s], J + J_offsets[s], reinterpret_cast<float *>(hJ.data()) + c->samples[s].J_off * js);
         }
         CK(cudaMemcpy(c->d_J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
     } else {

@@ -74,6 +74,9 @@ template <typename T> __host__ __device__ inline typename vec2<T>::type mk2(T x,
 // and the blocks of l are those of the s-tiles meeting [l, l+N-1]: a contiguous run of the sample's
 // block list.
 constexpr int TS = 8, TX = 8, TBLK = TS * TX;
+// A block is stored column-major ([i][r], i = x offset, r = s offset) followed by 16 bytes of padding,
+// so that blocks that sit next to each other in shared memory start in different banks.
+template <typename real> struct JStride { static constexpr int value = TBLK + 16 / (int)sizeof(real); };
 constexpr int APAD = 16;  // zero rows below and above the amplitude table in shared memory
 
 // Per-sample descriptor (device copy).

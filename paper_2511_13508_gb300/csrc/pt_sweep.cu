@@ -98,7 +98,7 @@ template <typename real, int G> struct RowStride {
     static constexpr int value = (sizeof(real) == 4 && G == 8) ? G + 1 : G;
 };
 
-// Loads one J row (TX reals) of a block as vectors.
+// Loads one J column (TS reals: fixed x offset, the TS rows) of a block as vectors.
 template <typename real> struct JRow;
 template <> struct JRow<float> {
     float v[TX];
@@ -126,8 +126,18 @@ template <typename real> struct Partials {
     }
 };
 
+// h += conj(m) acc, as four fused multiply-adds
+template <typename V> __device__ __forceinline__ void cfma_conj(V &h, V m, V acc) {
+    h.x = fma(m.x, acc.x, h.x);
+    h.x = fma(m.y, acc.y, h.x);
+    h.y = fma(m.x, acc.y, h.y);
+    h.y = fma(-m.y, acc.x, h.y);
+}
+
 // One TS x TX block of pair products for chain c: accumulates the j field (MODE & 1), the k field
-// (MODE & 2), and the j-k cross terms (with the j field).  as = shared amplitude table.
+// (MODE & 2), and the j-k cross terms (with the j field).  as = shared amplitude table; Jj, Jk =
+// column-major blocks.  The x offset i runs outside, the row r inside, so the 2*TS row accumulators
+// are independent chains of fused multiply-adds.
 template <typename real, int RS, int MODE>
 __device__ __forceinline__ void process_block(const typename vec2<real>::type *__restrict__ as, int c, int s0,
                                               int x0, int j, int k, int N, const real *Jj, const real *Jk,
@@ -139,29 +149,29 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
     const int ybase = s0 - x0 - (TX - 1) + APAD;
 #pragma unroll
     for (int d = 0; d < TS + TX - 1; ++d) ay[d] = as[(ybase + d) * RS + c];
+    V accj[TS], acck[TS];
+#pragma unroll
+    for (int r = 0; r < TS; ++r) accj[r].x = accj[r].y = acck[r].x = acck[r].y = real(0);
+#pragma unroll
+    for (int i = 0; i < TX; ++i) {
+        JRow<real> cj, ck;
+        if (MODE & 1) cj.load(Jj + i * TS);
+        if (MODE & 2) ck.load(Jk + i * TS);
+#pragma unroll
+        for (int r = 0; r < TS; ++r) {
+            const V z = cmul(ax[i], ay[r - i + TX - 1]);
+            if (MODE & 1) caxpy(accj[r], cj.v[r], z);
+            if (MODE & 2) caxpy(acck[r], ck.v[r], z);
+        }
+    }
 #pragma unroll
     for (int r = 0; r < TS; ++r) {
-        V accj, acck;
-        accj.x = accj.y = acck.x = acck.y = real(0);
-        JRow<real> rj, rk;
-        if (MODE & 1) rj.load(Jj + r * TX);
-        if (MODE & 2) rk.load(Jk + r * TX);
-#pragma unroll
-        for (int i = 0; i < TX; ++i) {
-            const V z = cmul(ax[i], ay[r - i + TX - 1]);
-            if (MODE & 1) caxpy(accj, rj.v[i], z);
-            if (MODE & 2) caxpy(acck, rk.v[i], z);
-        }
         const int s = s0 + r;
         if (MODE & 1) {
-            const V m = as[(s - j + APAD) * RS + c];
-            cadd(p.hj, cmulc(m, accj));
-            if (s == j + k) cadd(p.A, accj);
+            cfma_conj(p.hj, as[(s - j + APAD) * RS + c], accj[r]);
+            if (s == j + k) cadd(p.A, accj[r]);
         }
-        if (MODE & 2) {
-            const V m = as[(s - k + APAD) * RS + c];
-            cadd(p.hk, cmulc(m, acck));
-        }
+        if (MODE & 2) cfma_conj(p.hk, as[(s - k + APAD) * RS + c], acck[r]);
     }
     if (MODE & 1) {
         // B_jk: the element of row s at x* = min(k, s-k) belongs to this block for the rows s >= 2k of
@@ -174,11 +184,10 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
                 const int s = s0 + r, y = s - k;
                 const int xs = (y < k) ? y : k;
                 if (y >= 0 && y < N && xs >= x0 && xs < x0 + TX) {
-                    const real Jv = Jj[r * TX + (xs - x0)];
+                    const real Jv = Jj[(xs - x0) * TS + r];
                     const V m = as[(s - j + APAD) * RS + c];
-                    const V y = as[(s - k + APAD) * RS + c];
-                    const V t = cmulc(m, y);
-                    caxpy(p.B, Jv, t);
+                    const V yv = as[(y + APAD) * RS + c];
+                    caxpy(p.B, Jv, cmulc(m, yv));
                 }
             }
         }
@@ -300,7 +309,8 @@ template <typename real, int G, int NCW> struct SweepShape {
     static constexpr int NST = 3;
     static constexpr int RS = RowStride<real, G>::value;
     static constexpr int NTHREADS = (NCW + 1) * 32;
-    static constexpr size_t stage_bytes = (size_t)2 * CB * TBLK * sizeof(real);
+    static constexpr int JS = JStride<real>::value;
+    static constexpr size_t stage_bytes = (size_t)2 * CB * JS * sizeof(real);
 };
 
 template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
@@ -312,6 +322,7 @@ template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
     b += Sh::NST * Sh::stage_bytes;                                       // J ring
     b += (size_t)(maxN + 2 * APAD) * Sh::RS * sizeof(V);                  // amplitudes
     b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
+    b += (size_t)2 * G * sizeof(Proposal<real>) + 16;                     // proposals, double-buffered
     b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
     b += (size_t)(2 * 128 + 8) * sizeof(int);                             // bo / xtlo tables
     b += 64;
@@ -322,7 +333,7 @@ template <typename real, int G, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams prm) {
     using Sh = SweepShape<real, G, NCW>;
     using V = typename vec2<real>::type;
-    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW;
+    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS;
     constexpr int NCT = NCW * 32;  // consumer threads
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -335,6 +346,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     off += (size_t)(prm.maxN + 2 * APAD) * RS * sizeof(V);
     real *red = reinterpret_cast<real *>(smem + off);
     off += (size_t)2 * NCW * G * 8 * sizeof(real);
+    off = (off + 15) / 16 * 16;
+    Proposal<real> *prop = reinterpret_cast<Proposal<real> *>(smem + off);
+    off += (size_t)2 * G * sizeof(Proposal<real>);
     double *cE = reinterpret_cast<double *>(smem + off);
     off += G * sizeof(double);
     real *cBeta = reinterpret_cast<real *>(smem + off);
@@ -463,13 +477,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const int ce = min(cb + CB, Rg.uhi);
                             const int a0 = max(cb, Rg.jlo), a1 = min(ce, Rg.jhi);
                             const int b0 = max(cb, Rg.klo), b1 = min(ce, Rg.khi);
-                            const uint32_t bj = a1 > a0 ? (uint32_t)(a1 - a0) * TBLK * sizeof(real) : 0u;
-                            const uint32_t bk = b1 > b0 ? (uint32_t)(b1 - b0) * TBLK * sizeof(real) : 0u;
-                            real *st_j = ring + (size_t)stage * 2 * CB * TBLK;
-                            real *st_k = st_j + (size_t)CB * TBLK;
+                            const uint32_t bj = a1 > a0 ? (uint32_t)(a1 - a0) * JS * sizeof(real) : 0u;
+                            const uint32_t bk = b1 > b0 ? (uint32_t)(b1 - b0) * JS * sizeof(real) : 0u;
+                            real *st_j = ring + (size_t)stage * 2 * CB * JS;
+                            real *st_k = st_j + (size_t)CB * JS;
                             if (ok) mbar_arrive_expect_tx(&full[stage], bj + bk);
-                            if (ok && bj) bulk_g2s(st_j + (size_t)(a0 - cb) * TBLK, J + (Rg.jg + (a0 - Rg.jlo)) * TBLK, bj, &full[stage]);
-                            if (ok && bk) bulk_g2s(st_k + (size_t)(b0 - cb) * TBLK, J + (Rg.kg + (b0 - Rg.klo)) * TBLK, bk, &full[stage]);
+                            if (ok && bj) bulk_g2s(st_j + (size_t)(a0 - cb) * JS, J + (Rg.jg + (a0 - Rg.jlo)) * JS, bj, &full[stage]);
+                            if (ok && bk) bulk_g2s(st_k + (size_t)(b0 - cb) * JS, J + (Rg.kg + (b0 - Rg.klo)) * JS, bk, &full[stage]);
                         }
                         __syncwarp();
                     }
@@ -486,11 +500,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     int j, k;
                     pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
                     const Ranges Rg = update_ranges(sd, s_bo, mode_blk, j, k);
-                    // proposal for chain c (lanes of worker 0 of every warp, redundantly)
-                    Proposal<real> P;
-                    if (wq == 0) {
+                    // proposal for chain c, drawn by warp 0 into the double-buffered table
+                    Proposal<real> *Pp = prop + red_par * G;
+                    if (warp == 0 && wq == 0) {
                         const V aj = as[(j + APAD) * RS + c], ak = as[(k + APAD) * RS + c];
-                        P = make_proposal<real>(prm.seed, cId[c], sweep, (uint32_t)u, aj, ak);
+                        Pp[c] = make_proposal<real>(prm.seed, cId[c], sweep, (uint32_t)u, aj, ak);
                     }
                     Partials<real> pr;
                     pr.zero();
@@ -503,8 +517,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const uint32_t info = __ldg(binfo + b);
                             const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
                             const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
-                            const real *st_j = ring + (size_t)stage * 2 * CB * TBLK + (size_t)worker * TBLK;
-                            const real *st_k = st_j + (size_t)CB * TBLK;
+                            const real *st_j = ring + (size_t)stage * 2 * CB * JS + (size_t)worker * JS;
+                            const real *st_k = st_j + (size_t)CB * JS;
                             process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
                         }
                         __syncwarp();
@@ -522,24 +536,39 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                         for (int e = 0; e < 8; ++e) rb[(warp * G + c) * 8 + e] = v[e];
                     }
                     named_bar(1, NCT);
-                    if (wq == 0) {
-                        Partials<real> f;
-                        f.zero();
+                    {
+                        // every warp forms the same totals (fixed order) and takes the same decision
+                        // lane (c, wq) adds the partials of warps wq, wq + WPW, ...: the trip count is the
+                        // same on every lane (predicated body), so the warp is converged at the shuffles
                         real t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        for (int w = 0; w < NCW; ++w)
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) t[e] += rb[(w * G + c) * 8 + e];
-                        f.hj.x = t[0]; f.hj.y = t[1]; f.hk.x = t[2]; f.hk.y = t[3];
-                        f.B.x = t[4]; f.B.y = t[5]; f.A.x = t[6]; f.A.y = t[7];
-                        const real dH = delta_h<real>(P, f, cc);
-                        const bool acc = (c < gr.count) && metropolis_accept(dH, cBeta[c], P.U);
-                        if (acc) {
-                            as[(j + APAD) * RS + c] = P.nj;
-                            as[(k + APAD) * RS + c] = P.nk;
+                        for (int w0 = 0; w0 < NCW; w0 += WPW) {
+                            const int w = w0 + wq;
+                            if (w < NCW) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) t[e] += rb[(w * G + c) * 8 + e];
+                            }
                         }
-                        if (warp == 0 && c < gr.count) {
-                            if (acc) { cE[c] += (double)dH; cAcc[c] += 1u; }
-                            cAtt[c] += 1ull;
+                        __syncwarp();
+#pragma unroll
+                        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) t[e] += __shfl_xor_sync(0xffffffffu, t[e], o);
+                        if (wq == 0) {
+                            Partials<real> f;
+                            f.hj.x = t[0]; f.hj.y = t[1]; f.hk.x = t[2]; f.hk.y = t[3];
+                            f.B.x = t[4]; f.B.y = t[5]; f.A.x = t[6]; f.A.y = t[7];
+                            const Proposal<real> P = Pp[c];
+                            const real dH = delta_h<real>(P, f, cc);
+                            const bool acc = (c < gr.count) && metropolis_accept(dH, cBeta[c], P.U);
+                            if (acc) {
+                                as[(j + APAD) * RS + c] = P.nj;
+                                as[(k + APAD) * RS + c] = P.nk;
+                            }
+                            if (warp == 0 && c < gr.count) {
+                                if (acc) { cE[c] += (double)dH; cAcc[c] += 1u; }
+                                cAtt[c] += 1ull;
+                            }
                         }
                     }
                     red_par ^= 1;
@@ -625,8 +654,8 @@ __global__ void fields_kernel(FieldsParams prm) {
         const uint32_t info = prm.blkinfo[sd.blk_off + b];
         const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
         const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
-        const real *Jj = J + (Rg.jg + (b - Rg.jlo)) * TBLK;
-        const real *Jk = J + (Rg.kg + (b - Rg.klo)) * TBLK;
+        const real *Jj = J + (Rg.jg + (b - Rg.jlo)) * JStride<real>::value;
+        const real *Jk = J + (Rg.kg + (b - Rg.klo)) * JStride<real>::value;
         process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, Jj, Jk, pr);
     }
     real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
@@ -710,28 +739,31 @@ __global__ void energy_kernel(EnergyParams prm) {
         const int b = bo[sta] + (it - ebo[x]);
         const uint32_t info = prm.blkinfo[sd.blk_off + b];
         const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
-        const real *Jx = J + (sd.J_off + mode_blk[x] + (b - bo[stlo])) * TBLK;
+        const real *Jx = J + (sd.J_off + mode_blk[x] + (b - bo[stlo])) * JStride<real>::value;
         const int s0 = st * TS, x0 = xt * TX;
-        V ax[TX], ay[TS + TX - 1];
+        V ax[TX], ay[TS + TX - 1], acc[TS];
 #pragma unroll
         for (int i = 0; i < TX; ++i) ax[i] = as[(x0 + i + APAD) * RS + c];
         const int ybase = s0 - x0 - (TX - 1) + APAD;
 #pragma unroll
         for (int d = 0; d < TS + TX - 1; ++d) ay[d] = as[(ybase + d) * RS + c];
+#pragma unroll
+        for (int r = 0; r < TS; ++r) acc[r].x = acc[r].y = real(0);
+#pragma unroll
+        for (int i = 0; i < TX; ++i) {
+            JRow<real> jc;
+            jc.load(Jx + i * TS);
+#pragma unroll
+            for (int r = 0; r < TS; ++r) caxpy(acc[r], jc.v[r], cmul(ax[i], ay[r - i + TX - 1]));
+        }
         const V axx = as[(x + APAD) * RS + c];
         real blk = real(0);
 #pragma unroll
         for (int r = 0; r < TS; ++r) {
-            const int s = s0 + r, m = s - x;
+            const int m = s0 + r - x;
             if (m > x && m < N) {
-                JRow<real> jr;
-                jr.load(Jx + r * TX);
-                V acc; acc.x = acc.y = real(0);
-#pragma unroll
-                for (int i = 0; i < TX; ++i) caxpy(acc, jr.v[i], cmul(ax[i], ay[r - i + TX - 1]));
-                const V am = as[(m + APAD) * RS + c];
-                const V zz = cmul(axx, am);          // z_{x,m}
-                blk += zz.x * acc.x + zz.y * acc.y;  // Re(conj(z) acc)
+                const V zz = cmul(axx, as[(m + APAD) * RS + c]);  // z_{x,m}
+                blk += zz.x * acc[r].x + zz.y * acc[r].y;          // Re(conj(z) acc)
             }
         }
         e += (double)blk;
@@ -771,11 +803,13 @@ static int occupancy_t(int maxN) {
     return nb;
 }
 
-#define PT_SWEEP_VARIANTS(X)            \
-    X(float, 8, 8) X(float, 8, 16)      \
-    X(float, 16, 8) X(float, 16, 16)    \
-    X(float, 32, 4) X(float, 32, 8)     \
-    X(double, 8, 8) X(double, 16, 4)
+#define PT_SWEEP_VARIANTS(X)                        \
+    X(float, 8, 7) X(float, 8, 11) X(float, 8, 15)  \
+    X(float, 8, 12) X(float, 8, 13) X(float, 8, 14) \
+    X(float, 16, 14) X(float, 32, 14) X(float, 16, 15) \
+    X(float, 16, 7) X(float, 16, 11)                \
+    X(float, 32, 3) X(float, 32, 7)                 \
+    X(double, 8, 7) X(double, 16, 3)
 
 bool sweep_variant_exists(bool dbl, int G, int ncw) {
 #define X(T, g, n) if (dbl == (sizeof(T) == 8) && G == g && ncw == n) return true;
