@@ -56,6 +56,24 @@ def flops_per_chain_sweep(N: int) -> float:
     return tot / (N * (N - 1)) * (N / 2)
 
 
+def profiled_traffic():
+    """DRAM bytes per bench sweep launch from the committed ncu summary, or None if the kernel source changed
+    since the counters were taken."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "sweep_kernel_n256.md")).read()
+        src = open(os.path.join(ROOT, "paper_2511_13508_gb300", "csrc", "pt_sweep.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = hashlib.sha1(src).hexdigest()[:12]
+    if ("sha1 prefix `%s`" % sha) not in txt:
+        return None
+    for line in txt.splitlines():
+        if line.startswith("traffic_bytes_per_bench_launch:"):
+            return float(line.split(":")[1])
+    return None
+
+
 def peak_fp32_tflops(sm_count=152, mhz=2070.0):
     """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -303,8 +321,8 @@ def main():
                 "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
-                             "frac": r["achieved"] / r["peak"], "traffic": None,
-                             "kernel": "sweep_kernel<float,8,15> (8 chains x 15 field warps + 1 copy warp per block)", "kernel_ms_per_launch": r["kms"],
+                             "frac": r["achieved"] / r["peak"], "traffic": profiled_traffic(),
+                             "kernel": "sweep_kernel<float,8,11> (8 chains x 11 field warps + 1 copy warp per block)", "kernel_ms_per_launch": r["kms"],
                              "flops_per_launch": r["fl"],
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)"},
                 "cpu_baseline": cpu,

@@ -163,6 +163,12 @@ int pt_fields(pt_ctx *ctx, int sample, int j, int k, double *out);
 int pt_save(pt_ctx *ctx, void *buf, size_t *len);
 int pt_load(pt_ctx *ctx, const void *buf, size_t len);
 
+/* Autotuner of the sweep blocks (chains per block, field warps, sweeps per scheduling unit): times
+ * every supported shape for trial_sweeps sweeps on the live ensemble, keeps the fastest and restores
+ * the ensemble (state, counters, accumulators) exactly as before the call.  chosen (optional, 3 ints)
+ * receives {chains_per_block, consumer_warps, sweeps_per_unit}.  PT_EUNSUPPORTED for the plain path. */
+int pt_autotune(pt_ctx *ctx, int trial_sweeps, int *chosen);
+
 /* Counters: sweeps done since creation, swap passes done. */
 int pt_counters(pt_ctx *ctx, int64_t *sweeps_done, int64_t *swap_passes);
 

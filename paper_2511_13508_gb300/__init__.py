@@ -46,7 +46,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "pt_swap", "pt_resync",
            "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
-           "pt_fields", "pt_save", "pt_load", "pt_counters", "pt_sync", "pt_destroy", "pt_last_error"]
+           "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
+           "pt_last_error"]
 
 _lib = None
 
@@ -79,6 +80,7 @@ def lib() -> ctypes.CDLL:
         L.pt_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.pt_load.argtypes = [vp, vp, ctypes.c_size_t]
         L.pt_counters.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.pt_autotune.argtypes = [vp, i, vp]
         L.pt_last_error.argtypes = [vp]; L.pt_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -237,6 +239,13 @@ class PT:
     def load(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._c(lib().pt_load(self._h, buf, len(blob)))
+
+    def autotune(self, trial_sweeps=8):
+        """Times the supported sweep-block shapes on the live ensemble, keeps the fastest and restores
+        the ensemble; returns (chains_per_block, consumer_warps, sweeps_per_unit)."""
+        out = (ctypes.c_int * 3)()
+        self._c(lib().pt_autotune(self._h, int(trial_sweeps), out))
+        return tuple(out)
 
     @property
     def counters(self):

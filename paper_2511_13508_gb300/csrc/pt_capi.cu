@@ -175,6 +175,7 @@ struct pt_ctx {
     std::map<SegKey, cudaGraphExec_t> graphs;
     std::vector<cudaGraph_t> graph_defs;
     bool own_stream = false;
+    size_t max_groups = 0;  // capacity of d_groups / d_progress (groups of 8 chains)
 };
 
 namespace {
@@ -345,11 +346,43 @@ int run_segment(pt_ctx *c, const SegKey &k) {
     return PT_OK;
 }
 
-void free_all(pt_ctx *c) {
+// Chain groups of G chains per sample, the most expensive (largest N) first.
+void make_groups(pt_ctx *c, int G) {
+    c->groups.clear();
+    const int cps = c->R * c->nT;
+    for (int s = 0; s < c->S; ++s)
+        for (int g0 = 0; g0 < cps; g0 += G) c->groups.push_back({s, c->samples[s].chain0 + g0, std::min(G, cps - g0), 0});
+    std::stable_sort(c->groups.begin(), c->groups.end(),
+                     [&](const GroupDev &x, const GroupDev &y) { return c->N[x.sample] > c->N[y.sample]; });
+}
+
+void drop_graphs(pt_ctx *c) {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     for (auto g : c->graph_defs) cudaGraphDestroy(g);
     c->graphs.clear();
     c->graph_defs.clear();
+}
+
+// Switches the sweep blocks to G chains x ncw field warps (sweeps_per_unit spu); rebuilds the groups.
+int set_shape(pt_ctx *c, int G, int ncw, int spu) {
+    if (!sweep_variant_exists(c->dbl, G, ncw)) return fail(c, PT_EINVAL, "unsupported sweep block shape");
+    const int occ = sweep_occupancy(c->dbl, G, ncw, c->maxN);
+    if (occ < 1) return fail(c, PT_EUNSUPPORTED, "sweep block shape does not fit on this GPU");
+    make_groups(c, G);
+    if (c->groups.size() > c->max_groups) return fail(c, PT_EINVAL, "too many groups for this context");
+    CK(cudaMemcpy(c->d_groups, c->groups.data(), c->groups.size() * sizeof(GroupDev), cudaMemcpyHostToDevice));
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int bps = c->cfg.blocks_per_sm > 0 ? std::min(c->cfg.blocks_per_sm, occ) : occ;
+    c->grid = std::max(1, std::min((int)c->groups.size(), sms * bps));
+    c->G = G; c->ncw = ncw; c->spu = spu;
+    drop_graphs(c);
+    return PT_OK;
+}
+
+void free_all(pt_ctx *c) {
+    drop_graphs(c);
     for (auto &p : c->allocs) {
         if (c->free_) c->free_(p.first, c->user);
         else cudaFree(p.first);
@@ -462,15 +495,18 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
 
     // ---- scheduling shape
     const int chains_ps = replicas * n_T;
-    int G = cfg.chains_per_block, ncw = 8;
+    // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
+    // N >= 128: 8 chains x 11 warps; 48 <= N < 128: 32 x 7 when a sample has >= 32 chains; else 16 x 7
+    int G = cfg.chains_per_block, ncw = 0;
     if (G == 0) {
         if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
-        else G = (c->maxN >= 128) ? 8 : (c->maxN >= 48 ? 16 : 32);
+        else if (c->maxN >= 128) G = 8;
+        else if (c->maxN >= 48 && chains_ps >= 32) G = 32;
+        else G = 16;
         if (G > 8 && chains_ps <= 8) G = 8;
     }
-    // consumer warps: with the producer warp the block is a multiple of four warps
     if (c->dbl) ncw = (G == 16) ? 3 : 7;
-    else ncw = (G == 8) ? (c->maxN >= 128 ? 15 : 7) : (G == 16 ? 7 : 3);
+    else ncw = (G == 8) ? (c->maxN >= 128 ? 11 : 7) : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;
@@ -498,7 +534,6 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
         ebo_all.insert(ebo_all.end(), lay[s].ebo.begin(), lay[s].ebo.end());
         c->samples.push_back(sd);
         for (int i = 0; i < chains_ps; ++i) c->chain_sample.push_back(s);
-        for (int g0 = 0; g0 < chains_ps; g0 += G) c->groups.push_back({s, chain0 + g0, std::min(G, chains_ps - g0), 0});
         jblocks += lay[s].jblocks;
         a_off += (int64_t)c->N[s] * chains_ps;
         q_off += sd.nq;
@@ -508,11 +543,8 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
     // xtlo needs ST entries per sample at tab_off; pad to keep offsets aligned with bo (ST+1 entries)
     c->n_chains = chain0;
     c->a_total = a_off;
-    // expensive groups first (ragged batches): cost ~ N^3
-    std::stable_sort(c->groups.begin(), c->groups.end(), [&](const GroupDev &x, const GroupDev &y) {
-        return c->N[x.sample] > c->N[y.sample];
-    });
-
+    make_groups(c, G);
+    c->max_groups = (size_t)S * ((chains_ps + 7) / 8);
     // ---- schedule buffers
     int ev = 0;
     for (int e : {cfg.swap_every, cfg.resync_every}) if (e > 0) ev = ev ? std::min(ev, e) : e;
@@ -521,7 +553,7 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
 
     // ---- device memory
     RC(dalloc(c, &c->d_samples, S));
-    RC(dalloc(c, &c->d_groups, c->groups.size()));
+    RC(dalloc(c, &c->d_groups, c->max_groups));
     RC(dalloc(c, &c->d_bo, bo_all.size()));
     RC(dalloc(c, &c->d_xtlo, xtlo_all.size()));
     RC(dalloc(c, &c->d_blkinfo, std::max<size_t>(1, binfo_all.size())));
@@ -538,7 +570,7 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
     RC(dalloc(c, &c->d_label, c->n_chains));
     RC(dalloc(c, &c->d_perm, c->n_chains));
     RC(dalloc(c, &c->d_chain_sample, c->n_chains));
-    RC(dalloc(c, &c->d_progress, c->groups.size()));
+    RC(dalloc(c, &c->d_progress, c->max_groups));
     RC(dalloc(c, &c->d_mc_acc, c->n_chains));
     RC(dalloc(c, &c->d_mc_att, c->n_chains));
     RC(dalloc(c, &c->d_mcT_acc, (size_t)S * n_T));
@@ -955,6 +987,55 @@ int pt_load(pt_ctx *c, const void *buf, size_t len) {
     CK(cudaMemcpy(c->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
     c->sweeps_done = h.sweeps_done;
     c->swap_passes = h.swap_passes;
+    return PT_OK;
+}
+
+int pt_autotune(pt_ctx *c, int trial_sweeps, int *chosen) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_autotune: NULL context");
+    if (c->plain) return fail(c, PT_EUNSUPPORTED, "pt_autotune: the plain FP64 path has one shape");
+    if (trial_sweeps < 1) return fail(c, PT_EINVAL, "pt_autotune: trial_sweeps must be >= 1");
+    size_t len = 0;
+    int rc = pt_save(c, nullptr, &len);
+    if (rc != PT_OK) return rc;
+    std::vector<unsigned char> blob(len);
+    if ((rc = pt_save(c, blob.data(), &len)) != PT_OK) return rc;
+    const int cps = c->R * c->nT;
+    const int spu0 = c->cfg.sweeps_per_unit > 0 ? c->cfg.sweeps_per_unit
+                                                 : (c->maxN >= 192 ? 1 : c->maxN >= 96 ? 2 : c->maxN >= 48 ? 8 : 32);
+    struct Cand { int G, ncw, spu; };
+    std::vector<Cand> cands;
+    const int Gs_f[] = {8, 16, 32}, Gs_d[] = {8, 16};
+    const int ncws[] = {3, 7, 11, 15};
+    for (int G : (c->dbl ? std::vector<int>(Gs_d, Gs_d + 2) : std::vector<int>(Gs_f, Gs_f + 3))) {
+        if (G > 8 && cps < G / 2) continue;  // mostly empty blocks
+        for (int n : ncws)
+            if (sweep_variant_exists(c->dbl, G, n))
+                for (int sp : {spu0, spu0 * 4}) cands.push_back({G, n, sp});
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand bestc = {c->G, c->ncw, c->spu};
+    for (const Cand &cd : cands) {
+        if (set_shape(c, cd.G, cd.ncw, cd.spu) != PT_OK) continue;
+        if ((rc = pt_sweep(c, 1)) != PT_OK) break;  // warm-up (graph capture)
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) break;
+        if ((rc = pt_sweep(c, trial_sweeps)) != PT_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess) break;
+        if ((rc = watchdog_sync(c)) != PT_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bestc = cd; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rc2 = set_shape(c, bestc.G, bestc.ncw, bestc.spu);
+    const int rc3 = pt_load(c, blob.data(), len);  // the trials leave no trace
+    if (rc != PT_OK) return rc;
+    if (rc2 != PT_OK) return rc2;
+    if (rc3 != PT_OK) return rc3;
+    if (chosen) { chosen[0] = bestc.G; chosen[1] = bestc.ncw; chosen[2] = bestc.spu; }
     return PT_OK;
 }
 

@@ -167,11 +167,17 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
 #pragma unroll
     for (int r = 0; r < TS; ++r) {
         const int s = s0 + r;
-        if (MODE & 1) {
-            cfma_conj(p.hj, as[(s - j + APAD) * RS + c], accj[r]);
-            if (s == j + k) cadd(p.A, accj[r]);
-        }
+        if (MODE & 1) cfma_conj(p.hj, as[(s - j + APAD) * RS + c], accj[r]);
         if (MODE & 2) cfma_conj(p.hk, as[(s - k + APAD) * RS + c], acck[r]);
+    }
+    if (MODE & 1) {
+        // A_jk is the accumulator of row j+k: only the blocks of that row's s-tile hold it
+        const int rs = j + k - s0;
+        if (rs >= 0 && rs < TS) {
+#pragma unroll
+            for (int r = 0; r < TS; ++r)
+                if (r == rs) cadd(p.A, accj[r]);
+        }
     }
     if (MODE & 1) {
         // B_jk: the element of row s at x* = min(k, s-k) belongs to this block for the rows s >= 2k of
