@@ -181,6 +181,14 @@ int pt_destroy(pt_ctx *ctx);
 /* Message of the last failing call on ctx (or of the last failing pt_create when ctx is NULL). */
 const char *pt_last_error(const pt_ctx *ctx);
 
+/* Batched tensor-core GEMM used by the learned global-move proposal (the paper has none): for every
+ * b < batch, D[b] = A[b] * B[b]^T with A[b] an M x K and B[b] an N x K row-major BF16 matrix
+ * (device pointers, batches back to back) and D[b] an M x N row-major FP32 matrix, accumulated in FP32
+ * on the sm_100-class tensor cores (tcgen05.mma, accumulator in tensor memory).  Constraints:
+ * 16 <= N <= 256, N % 16 == 0, K % 8 == 0, K >= 16.  Asynchronous on stream.  PT_EINVAL / PT_ECUDA;
+ * message in pt_last_error(NULL). */
+int pt_gemm_bf16(int batch, int M, int N, int K, const void *A, const void *B, float *D, void *stream);
+
 /* Allocation-free FP64 energies of a batch of chains.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory (a program whose device memory belongs to
  * another runtime's pool, a real-time loop where cudaMalloc/cudaFree would synchronise the device, a

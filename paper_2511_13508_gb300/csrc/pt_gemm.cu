@@ -1,0 +1,202 @@
+// pt_gemm.cu -- batched BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, TMEM)
+// for the learned global-move proposal's network (the paper has no counterpart; the proposal serves
+// the Parallel-Tempering path of arXiv 2511.13508).
+//
+//   D[b] (M x N, FP32) = A[b] (M x K, BF16, row-major = K-major) * B[b]^T (B: N x K, BF16, K-major)
+//
+// One thread block computes a 128 x N tile (N <= 256) with the accumulator in tensor memory: the
+// operands are staged in shared memory in the canonical K-major no-swizzle layout (8 x 16-byte core
+// matrices), one elected thread issues tcgen05.mma (M = 128, N, K = 16 per instruction) and commits to
+// an mbarrier, and four warps read the accumulator back with tcgen05.ld (warp w owns lanes 32w..32w+31)
+// for the epilogue.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include "pt_common.cuh"
+#include "pt_gemm.h"
+
+namespace ptgb {
+
+namespace {
+
+constexpr int kGemmM = 128;   // rows per thread block (= TMEM lanes)
+constexpr int kGemmKC = 64;   // K per shared-memory chunk (4 MMAs of K = 16)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, leading-dimension byte offset
+// (between core matrices adjacent in K), stride-dimension byte offset (between 8-row groups), version 1.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3fffu);
+    d |= (uint64_t)((lbo >> 4) & 0x3fffu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3fffu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for sm_100-class tensor cores
+    return d;                 // base offset 0, layout type 0 = no swizzle
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N.
+__device__ __forceinline__ uint32_t make_idesc(int N) {
+    uint32_t d = 0;
+    d |= 1u << 4;                          // D format F32
+    d |= 1u << 7;                          // A format BF16
+    d |= 1u << 10;                         // B format BF16
+    d |= (uint32_t)(N >> 3) << 17;         // N / 8
+    d |= (uint32_t)(kGemmM >> 4) << 24;    // M / 16
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Copies rows [r0, r0+rows) x K-chunk [k0, k0+KC) of a row-major BF16 matrix (leading dimension ld,
+// valid rows < nrows, valid columns < K) into the canonical layout: element (r, k) at
+// (k / 8) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes.  Out-of-range parts are zero.
+__device__ __forceinline__ void stage_tile(unsigned char *dst, const __nv_bfloat16 *src, int ld, int r0, int rows,
+                                          int nrows, int k0, int K, uint32_t lbo) {
+    const int pieces = rows * (kGemmKC / 8);
+    for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
+        const int r = p / (kGemmKC / 8), kg = p % (kGemmKC / 8);
+        const int gr = r0 + r, gk = k0 + kg * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < nrows && gk < K) v = *reinterpret_cast<const uint4 *>(src + (int64_t)gr * ld + gk);
+        *reinterpret_cast<uint4 *>(dst + kg * lbo + (r / 8) * 128 + (r % 8) * 16) = v;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(GemmParams p) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base_slot;
+    const int b = blockIdx.z, m0 = blockIdx.x * kGemmM;
+    const int N = p.N, K = p.K;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    unsigned char *sA = gsm;                                   // 128 x 64 BF16 = 16 KB
+    unsigned char *sB = gsm + kGemmM * kGemmKC * 2;            // N x 64 BF16 <= 32 KB
+    const uint32_t lboA = (kGemmM / 8) * 128, lboB = (uint32_t)((N + 7) / 8) * 128;
+    const __nv_bfloat16 *A = p.A + (int64_t)b * p.strideA;
+    const __nv_bfloat16 *Bm = p.B + (int64_t)b * p.strideB;
+
+    // tensor-memory accumulator: 256 columns x 128 lanes of FP32
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_base_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) mbar_init1(&mbar);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_slot;
+    const uint32_t idesc = make_idesc(N);
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    for (int k0 = 0; k0 < K; k0 += kGemmKC) {
+        stage_tile(sA, A, p.lda, m0, kGemmM, p.M, k0, K, lboA);
+        stage_tile(sB, Bm, p.ldb, 0, N, N, k0, K, lboB);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int ksteps = min(kGemmKC, K - k0 + 15) / 16;
+            for (int t = 0; t < ksteps && t < kGemmKC / 16; ++t) {
+                const uint64_t da = make_sdesc(smem_addr(sA) + t * 2 * lboA, lboA, 128);
+                const uint64_t db = make_sdesc(smem_addr(sB) + t * 2 * lboB, lboB, 128);
+                const uint32_t acc = (k0 > 0 || t > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred pacc;\n\tsetp.ne.b32 pacc, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pacc;\n\t}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar))
+                         : "memory");
+        }
+        // wait for the MMAs (bounded); every thread polls so the shared tiles may be overwritten after
+        const unsigned long long t0 = global_ns();
+        while (!mbar_test(&mbar, phase)) {
+            if (global_ns() - t0 > kWaitNs) { timed_out = true; break; }
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (timed_out && threadIdx.x == 0 && p.err) atomicCAS(p.err, 0, kErrTimeout);
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane, 32 columns at a time
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < p.M) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int col = c0 + q;
+                if (col < N) gemm_epilogue(p, b, row, col, __uint_as_float(r[q]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s) {
+    if (p.N < 16 || p.N > 256 || (p.N % 16) || p.K < 16 || (p.K % 8) || p.M < 1 || batch < 1)
+        return cudaErrorInvalidValue;
+    const size_t sm = (size_t)kGemmM * kGemmKC * 2 + (size_t)256 * kGemmKC * 2;
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.M + kGemmM - 1) / kGemmM, 1, batch);
+    gemm_bf16_tc_kernel<<<grid, 128, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace ptgb
+
+// ------------------------------------------------------------------------------------------------
+// C ABI: plain batched D = A B^T (see include/pt.h)
+#include "../../include/pt.h"
+namespace ptgb { void set_global_error(const char *msg); }
+
+extern "C" int pt_gemm_bf16(int batch, int M, int N, int K, const void *A, const void *B, float *D, void *stream) {
+    if (batch < 1 || M < 1 || N < 16 || N > 256 || (N % 16) || K < 16 || (K % 8) || !A || !B || !D) {
+        ptgb::set_global_error("pt_gemm_bf16: need batch, M >= 1, 16 <= N <= 256 with N % 16 == 0, K >= 16 with K % 8 == 0");
+        return PT_EINVAL;
+    }
+    ptgb::GemmParams p{};
+    p.A = reinterpret_cast<const __nv_bfloat16 *>(A);
+    p.B = reinterpret_cast<const __nv_bfloat16 *>(B);
+    p.strideA = (int64_t)M * K; p.strideB = (int64_t)N * K;
+    p.lda = K; p.ldb = K; p.M = M; p.N = N; p.K = K; p.mode = ptgb::kEpiF32;
+    p.D = D; p.strideD = (int64_t)M * N; p.ldd = N;
+    const cudaError_t e = ptgb::launch_gemm_bf16(p, batch, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        ptgb::set_global_error(cudaGetErrorString(e));
+        return PT_ECUDA;
+    }
+    return PT_OK;
+}

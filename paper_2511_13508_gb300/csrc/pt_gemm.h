@@ -1,0 +1,56 @@
+// pt_gemm.h -- batched BF16 tensor-core GEMM (tcgen05) with the epilogues of the proposal network.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ptgb {
+
+enum GemmEpilogue : int {
+    kEpiF32 = 0,   // D = acc (+ bias)
+    kEpiRelu = 1,  // z = acc + bias + cbias[cond[row]]; D = z; H = HT = bf16(max(z, 0))
+    kEpiGate = 2,  // g = acc * [gate > 0]; D = g; H = HT = bf16(g)   (back-propagation through a ReLU)
+};
+
+struct GemmParams {
+    const __nv_bfloat16 *A, *B;  // A: M x K row-major (lda); B: N x K row-major (ldb); per batch strides
+    int64_t strideA, strideB;
+    int lda, ldb, M, N, K, mode;
+    float *D;                    // optional FP32 output, M x N (ldd)
+    int64_t strideD;
+    int ldd;
+    const float *bias;           // optional, N per batch
+    int64_t strideBias;
+    const float *cbias;          // optional, [n_cond][N] per batch, row r uses cond[r]
+    int64_t strideCbias;
+    const int *cond;             // per batch, M entries (stride M_cond)
+    int64_t strideCond;
+    __nv_bfloat16 *H;            // optional BF16 output, M x N (ldh)
+    int64_t strideH;
+    int ldh;
+    __nv_bfloat16 *HT;           // optional BF16 transposed output, N x M (ldht)
+    int64_t strideHT;
+    int ldht;
+    const float *gate;           // for kEpiGate: M x N (ldgate)
+    int64_t strideGate;
+    int ldgate;
+    int *err;
+};
+
+__device__ __forceinline__ void gemm_epilogue(const GemmParams &p, int b, int row, int col, float v) {
+    if (p.mode == kEpiGate) {
+        const float g = p.gate[(int64_t)b * p.strideGate + (int64_t)row * p.ldgate + col];
+        v = g > 0.f ? v : 0.f;
+    } else {
+        if (p.bias) v += p.bias[(int64_t)b * p.strideBias + col];
+        if (p.cbias) v += p.cbias[(int64_t)b * p.strideCbias + (int64_t)p.cond[(int64_t)b * p.strideCond + row] * p.N + col];
+    }
+    if (p.D) p.D[(int64_t)b * p.strideD + (int64_t)row * p.ldd + col] = v;
+    if (p.mode == kEpiRelu) v = fmaxf(v, 0.f);
+    if (p.H) p.H[(int64_t)b * p.strideH + (int64_t)row * p.ldh + col] = __float2bfloat16_rn(v);
+    if (p.HT) p.HT[(int64_t)b * p.strideHT + (int64_t)col * p.ldht + row] = __float2bfloat16_rn(v);
+}
+
+cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s);
+
+}  // namespace ptgb
