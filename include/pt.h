@@ -91,6 +91,8 @@ typedef struct pt_observables {
     uint64_t *swap_att;
     uint64_t *mc_acc;
     uint64_t *mc_att;
+    uint64_t *gm_acc;   /* [S][n_T] learned global moves accepted / attempted (zero without them) */
+    uint64_t *gm_att;
 } pt_observables;
 
 /* Canonical quadruplet list of the N-mode comb (paper Sec. II.C "Graph generation"; Eq. (1) with
@@ -168,6 +170,55 @@ int pt_load(pt_ctx *ctx, const void *buf, size_t len);
  * the ensemble (state, counters, accumulators) exactly as before the call.  chosen (optional, 3 ints)
  * receives {chains_per_block, consumer_warps, sweeps_per_unit}.  PT_EUNSUPPORTED for the plain path. */
 int pt_autotune(pt_ctx *ctx, int trial_sweeps, int *chosen);
+
+/* ---- Learned global-move proposal (built for this engine; the paper has none).  A per-sample masked,
+ * block-autoregressive MLP (two hidden layers of 256, BF16 weights on the tensor cores, FP32 accumulate
+ * and FP32 master weights with Adam) gives a normalised density q over gauge-fixed coordinates: global
+ * phase and comb gauge removed (phi~_0 = phi~_1 = 0), intensity fractions s_k = |a_k|^4/N stick-broken into
+ * logit-normal v_k, phases phi~_k wrapped Cauchy, conditioned on the temperature index among the n_cold
+ * coldest.  A global move replaces a cold chain's configuration by a draw from q with a fresh uniform
+ * gauge and accepts it with the exact Metropolis-Hastings ratio
+ *   log A = -beta (H' - H) + [log q(x) + extra(x)] - [log q(x') + extra(x')],
+ * where log q is the log density of (v_k, phi~_k) and extra = -sum_{k<=N-2} log r_k + 1/2 sum_k log s_k
+ * (r_k = sum_{i>=k} s_i) turns it into the density on the constraint surface relative to the beta = 0 law
+ * of Eq. (8), prod_k s_k^(-1/2) ds dphi; so the tempered target stays invariant whatever the network has
+ * learned.  All samples must share one N in {16, 32, 48, 64}.
+ *
+ * pt_learn_init: allocates the networks and buffers.  n_cold: temperatures 0..n_cold-1 are conditioned
+ *   and moved; batch: training rows per sample and step (multiple of 128); data_per_sample: capacity of
+ *   the training set; seed: initial weights.  PT_EUNSUPPORTED for other N. */
+int pt_learn_init(pt_ctx *ctx, int n_cold, int batch, int data_per_sample, uint64_t seed);
+
+/* Runs `rounds` times: `every` sweeps (full schedule), then appends the configurations of the chains at the
+ * n_cold coldest temperatures (n_cold * R per sample) to the training set, until it is full. */
+int pt_collect(pt_ctx *ctx, int64_t every, int rounds);
+
+/* `steps` Adam steps (learning rate lr) on the mean negative log-likelihood of random minibatches of the
+ * training set.  losses (optional, steps doubles): mean -log q on the constraint surface per step. */
+int pt_train(pt_ctx *ctx, int steps, double lr, double *losses);
+
+/* One round of global moves on the n_cold coldest temperatures of every ladder (asynchronous). */
+int pt_global_move(pt_ctx *ctx);
+
+/* Schedules a round of global moves every `every` sweeps inside pt_sweep (0 = off); it runs after the
+ * resync and before the measurement of the same sweep. */
+int pt_set_global_every(pt_ctx *ctx, int every);
+
+/* FP32 master parameters of all samples, [S][psize] (layout from pt_learn_shape): set != 0 uploads them
+ * (and refreshes the BF16 copies), set == 0 downloads them. */
+int pt_learn_params(pt_ctx *ctx, float *params, int set);
+
+/* 14 int64: N, H, Din, Dout, n_cold, psize, offsets of W1 [H][Din], b1 [H], C1 [n_cold][H], W2 [H][H], b2,
+ * W3 [Dout][H], b3 [Dout] within one sample's parameters, and the number of collected configurations. */
+int pt_learn_shape(pt_ctx *ctx, int64_t *out);
+
+/* Evaluates the proposal on given configurations: a = [S][rows][N] interleaved complex doubles, cond =
+ * [S][rows] temperature indices (< n_cold).  logq [S][rows] receives log q (network part), extra (optional)
+ * [S][rows] the coordinate terms -sum log r_k + 1/2 sum log s_k (log q + extra = log density on the
+ * constraint surface), grad (optional, [S][psize] floats, rows % 8 == 0) the gradient of the mean over the
+ * rows of -log q with respect to the parameters.  rows <= max(batch, n_cold * R rounded up to 128). */
+int pt_learn_eval(pt_ctx *ctx, const double *a, const int *cond, int rows, double *logq, double *extra,
+                  float *grad);
 
 /* Counters: sweeps done since creation, swap passes done. */
 int pt_counters(pt_ctx *ctx, int64_t *sweeps_done, int64_t *swap_passes);

@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
 
 
 class Observables(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc", "mc_att")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc", "mc_att",
+                                               "gm_acc", "gm_att")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -47,7 +48,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "pt_swap", "pt_resync",
            "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
            "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
-           "pt_last_error"]
+           "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
+           "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_gemm_bf16", "pt_energy_fp64_static"]
 
 _lib = None
 
@@ -81,6 +83,16 @@ def lib() -> ctypes.CDLL:
         L.pt_load.argtypes = [vp, vp, ctypes.c_size_t]
         L.pt_counters.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.pt_autotune.argtypes = [vp, i, vp]
+        L.pt_learn_init.argtypes = [vp, i, i, i, u64]
+        L.pt_collect.argtypes = [vp, i64, i]
+        L.pt_train.argtypes = [vp, i, d, vp]
+        L.pt_global_move.argtypes = [vp]
+        L.pt_set_global_every.argtypes = [vp, i]
+        L.pt_learn_params.argtypes = [vp, vp, i]
+        L.pt_learn_shape.argtypes = [vp, vp]
+        L.pt_learn_eval.argtypes = [vp, vp, vp, i, vp, vp, vp]
+        L.pt_gemm_bf16.argtypes = [i, i, i, i, vp, vp, vp, vp]
+        L.pt_energy_fp64_static.argtypes = [i, i, vp, vp, vp, d, vp]
         L.pt_last_error.argtypes = [vp]; L.pt_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -201,8 +213,10 @@ class PT:
         o = dict(stat=np.zeros((S, nT, NSTAT)), qstat=np.zeros((S, nT, NQSTAT)),
                  qhist=np.zeros((S, nT, QBINS), np.uint64), swap_acc=np.zeros((S, R, np1), np.uint64),
                  swap_att=np.zeros((S, R, np1), np.uint64), mc_acc=np.zeros((S, nT), np.uint64),
-                 mc_att=np.zeros((S, nT), np.uint64))
-        ob = Observables(*[o[k].ctypes.data for k in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc", "mc_att")])
+                 mc_att=np.zeros((S, nT), np.uint64), gm_acc=np.zeros((S, nT), np.uint64),
+                 gm_att=np.zeros((S, nT), np.uint64))
+        ob = Observables(*[o[k].ctypes.data for k in ("stat", "qstat", "qhist", "swap_acc", "swap_att", "mc_acc",
+                                                      "mc_att", "gm_acc", "gm_att")])
         self._c(lib().pt_measure(self._h, ctypes.byref(ob)))
         return o
 
@@ -246,6 +260,51 @@ class PT:
         out = (ctypes.c_int * 3)()
         self._c(lib().pt_autotune(self._h, int(trial_sweeps), out))
         return tuple(out)
+
+    # ------------------------------------------------------------------ learned global-move proposal
+    def learn_init(self, n_cold=8, batch=512, data_per_sample=1 << 14, seed=0):
+        self._c(lib().pt_learn_init(self._h, int(n_cold), int(batch), int(data_per_sample), ctypes.c_uint64(int(seed))))
+
+    def learn_shape(self) -> dict:
+        out = np.zeros(14, np.int64)
+        self._c(lib().pt_learn_shape(self._h, _p(out)))
+        keys = ("N", "H", "Din", "Dout", "ncold", "psize", "oW1", "ob1", "oC1", "oW2", "ob2", "oW3", "ob3", "ndata")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def collect(self, every, rounds):
+        self._c(lib().pt_collect(self._h, int(every), int(rounds)))
+
+    def train(self, steps, lr=1e-3):
+        losses = np.zeros(max(int(steps), 1))
+        self._c(lib().pt_train(self._h, int(steps), float(lr), _p(losses)))
+        return losses[: int(steps)]
+
+    def global_move(self):
+        self._c(lib().pt_global_move(self._h))
+
+    def set_global_every(self, every):
+        self._c(lib().pt_set_global_every(self._h, int(every)))
+
+    def learn_params(self) -> np.ndarray:
+        sh = self.learn_shape()
+        P = np.zeros((self.S, sh["psize"]), np.float32)
+        self._c(lib().pt_learn_params(self._h, _p(P), 0))
+        return P
+
+    def set_learn_params(self, P):
+        P = np.ascontiguousarray(P, np.float32)
+        self._c(lib().pt_learn_params(self._h, _p(P), 1))
+
+    def learn_eval(self, a, cond, grad=False):
+        """a: [S, rows, N] complex; cond: [S, rows] -> (logq [S, rows], extra [S, rows], grad [S, psize] or None)."""
+        a = np.ascontiguousarray(a, np.complex128)
+        cond = np.ascontiguousarray(cond, np.int32)
+        S, rows = cond.shape
+        logq = np.zeros((S, rows)); extra = np.zeros((S, rows))
+        g = np.zeros((S, self.learn_shape()["psize"]), np.float32) if grad else None
+        self._c(lib().pt_learn_eval(self._h, _p(a), _p(cond), int(rows), _p(logq), _p(extra),
+                                     _p(g) if grad else None))
+        return logq, extra, g
 
     @property
     def counters(self):

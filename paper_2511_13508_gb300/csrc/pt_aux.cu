@@ -329,13 +329,14 @@ cudaError_t launch_plain_energy(const PlainParams &p, int n_chains, cudaStream_t
     return cudaGetLastError();
 }
 
-__global__ void advance_kernel(Control *ctl, long long sweeps, long long passes) {
+__global__ void advance_kernel(Control *ctl, long long sweeps, long long passes, long long rounds) {
     ctl->sweep_base += sweeps;
     ctl->swap_passes += passes;
+    ctl->global_rounds += rounds;
 }
 
-cudaError_t launch_advance(Control *ctl, long long sweeps, long long passes, cudaStream_t s) {
-    advance_kernel<<<1, 1, 0, s>>>(ctl, sweeps, passes);
+cudaError_t launch_advance(Control *ctl, long long sweeps, long long passes, long long rounds, cudaStream_t s) {
+    advance_kernel<<<1, 1, 0, s>>>(ctl, sweeps, passes, rounds);
     return cudaGetLastError();
 }
 

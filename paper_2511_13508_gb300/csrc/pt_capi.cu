@@ -15,7 +15,9 @@
 
 #include "../../include/pt.h"
 #include "pt_common.cuh"
+#include "pt_gemm.h"
 #include "pt_kernels.h"
+#include "pt_learn.h"
 
 using namespace ptgb;
 
@@ -125,10 +127,34 @@ void pack_sample(const SampleLayout &L, const double *J, real *dst) {
 }
 
 struct SegKey {
-    int seg, n_snap, resync, live, swap;
+    int seg, n_snap, resync, live, swap, global;
     bool operator<(const SegKey &o) const {
-        return std::tie(seg, n_snap, resync, live, swap) < std::tie(o.seg, o.n_snap, o.resync, o.live, o.swap);
+        return std::tie(seg, n_snap, resync, live, swap, global) <
+               std::tie(o.seg, o.n_snap, o.resync, o.live, o.swap, o.global);
     }
+};
+
+// Learned global-move proposal: network parameters, training set and work buffers (device memory).
+struct LearnState {
+    ptgb::LearnShape sh{};
+    int Mb = 0, ncap = 0, ndata = 0, nprop = 0, rows = 0, global_every = 0, adam_t = 0;
+    uint32_t step = 0;
+    uint64_t seed = 0;
+    float *P = nullptr, *Gr = nullptr, *Am = nullptr, *Av = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
+    __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2T = nullptr, *W3T = nullptr;
+    float *du = nullptr, *dphi = nullptr, *dextra = nullptr;
+    int *dcond = nullptr;
+    __nv_bfloat16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *H2T = nullptr;
+    __nv_bfloat16 *dOb = nullptr, *dOT = nullptr, *dZ2b = nullptr, *dZ2T = nullptr, *dZ1T = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *O = nullptr, *dO = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    ptgb::RawRows raw{}, rcur{}, rprop{}, rsamp{};
+    double *logq = nullptr, *lq_cur = nullptr, *lq_prop = nullptr, *H_cur = nullptr, *H_prop = nullptr;
+    int *pslot = nullptr, *pcond = nullptr;
+    uint32_t *prow = nullptr;
+    __nv_bfloat16 *Xp = nullptr;
+    double2 *a_prop = nullptr;
+    double *losses = nullptr;
+    int max_losses = 0;
 };
 
 }  // namespace
@@ -144,7 +170,7 @@ struct pt_ctx {
     pt_free_fn free_ = nullptr;
     void *user = nullptr;
     std::string err;
-    int64_t sweeps_done = 0, swap_passes = 0;
+    int64_t sweeps_done = 0, swap_passes = 0, global_rounds = 0;
     int n_chains = 0;
     int64_t a_total = 0;
     size_t esize = 8;  // bytes of one real
@@ -176,6 +202,8 @@ struct pt_ctx {
     std::vector<cudaGraph_t> graph_defs;
     bool own_stream = false;
     size_t max_groups = 0;  // capacity of d_groups / d_progress (groups of 8 chains)
+    LearnState *learn = nullptr;
+    unsigned long long *d_gm_acc = nullptr, *d_gm_att = nullptr;  // [S][nT] global-move counters
 };
 
 namespace {
@@ -311,14 +339,171 @@ int run_sweeps(pt_ctx *c, int seg) {
     return PT_OK;
 }
 
-// One segment: seg sweeps, then resync / measure / swap as due at its end.
+
+// ------------------------------------------------------------------------------------------- learned proposal
+template <typename T> T *lalloc(pt_ctx *c, size_t count, int *rc) {
+    T *p = reinterpret_cast<T *>(dev_alloc(c, count * sizeof(T)));
+    if (!p && *rc == PT_OK) *rc = fail(c, PT_ENOMEM, "device allocation failed (learned proposal)");
+    return p;
+}
+
+// Dense layers on the tensor cores: O = W3 relu(W2 relu(W1 x + b1 + C1[cond]) + b2) + b3 for `rows` rows of
+// every sample; with `train` the transposed activations the weight gradients need are kept as well.
+int learn_forward(pt_ctx *c, const __nv_bfloat16 *X, int rows, const int *cond, int64_t strideCond, bool train) {
+    LearnState &L = *c->learn;
+    const ptgb::LearnShape &sh = L.sh;
+    const int64_t rc = L.rows;
+    GemmParams g{};
+    g.A = X; g.strideA = rc * sh.Din; g.lda = sh.Din;
+    g.B = L.W1; g.strideB = (int64_t)sh.H * sh.Din; g.ldb = sh.Din;
+    g.M = rows; g.N = sh.H; g.K = sh.Din; g.mode = kEpiRelu;
+    g.D = L.Z1; g.strideD = rc * sh.H; g.ldd = sh.H;
+    g.bias = L.P + sh.ob1; g.strideBias = (int64_t)sh.psize;
+    g.cbias = L.P + sh.oC1; g.strideCbias = (int64_t)sh.psize; g.cond = cond; g.strideCond = strideCond;
+    g.H = L.H1; g.strideH = rc * sh.H; g.ldh = sh.H;
+    g.HT = train ? L.H1T : nullptr; g.strideHT = rc * sh.H; g.ldht = (int)rc;
+    g.err = &c->d_ctl->error;
+    CK(launch_gemm_bf16(g, c->S, c->stream));
+    GemmParams g2 = g;
+    g2.A = L.H1; g2.strideA = rc * sh.H; g2.lda = sh.H;
+    g2.B = L.W2; g2.strideB = (int64_t)sh.H * sh.H; g2.ldb = sh.H; g2.K = sh.H;
+    g2.D = L.Z2; g2.bias = L.P + sh.ob2; g2.cbias = nullptr; g2.cond = nullptr;
+    g2.H = L.H2; g2.HT = train ? L.H2T : nullptr;
+    CK(launch_gemm_bf16(g2, c->S, c->stream));
+    GemmParams g3{};
+    g3.A = L.H2; g3.strideA = rc * sh.H; g3.lda = sh.H;
+    g3.B = L.W3; g3.strideB = (int64_t)sh.Dout * sh.H; g3.ldb = sh.H;
+    g3.M = rows; g3.N = sh.Dout; g3.K = sh.H; g3.mode = kEpiF32;
+    g3.D = L.O; g3.strideD = rc * sh.Dout; g3.ldd = sh.Dout;
+    g3.bias = L.P + sh.ob3; g3.strideBias = (int64_t)sh.psize;
+    g3.err = &c->d_ctl->error;
+    CK(launch_gemm_bf16(g3, c->S, c->stream));
+    return PT_OK;
+}
+
+// Gradient of mean(-log q) over `rows` rows (dO already written by the density kernel) into L.Gr.
+int learn_backward(pt_ctx *c, int rows, const int *cond) {
+    LearnState &L = *c->learn;
+    const ptgb::LearnShape &sh = L.sh;
+    const int64_t rc = L.rows, ps = (int64_t)sh.psize;
+    CK(cudaMemsetAsync(L.Gr, 0, sizeof(float) * sh.psize * c->S, c->stream));
+    GemmParams g{};  // dZ2 = (dO W3) * [Z2 > 0]
+    g.A = L.dOb; g.strideA = rc * sh.Dout; g.lda = sh.Dout;
+    g.B = L.W3T; g.strideB = (int64_t)sh.H * sh.Dout; g.ldb = sh.Dout;
+    g.M = rows; g.N = sh.H; g.K = sh.Dout; g.mode = kEpiGate;
+    g.gate = L.Z2; g.strideGate = rc * sh.H; g.ldgate = sh.H;
+    g.D = L.dZ2; g.strideD = rc * sh.H; g.ldd = sh.H;
+    g.H = L.dZ2b; g.strideH = rc * sh.H; g.ldh = sh.H;
+    g.HT = L.dZ2T; g.strideHT = rc * sh.H; g.ldht = (int)rc;
+    g.err = &c->d_ctl->error;
+    CK(launch_gemm_bf16(g, c->S, c->stream));
+    GemmParams w3{};  // dW3 = dO^T H2
+    w3.A = L.dOT; w3.strideA = rc * sh.Dout; w3.lda = (int)rc;
+    w3.B = L.H2T; w3.strideB = rc * sh.H; w3.ldb = (int)rc;
+    w3.M = sh.Dout; w3.N = sh.H; w3.K = rows; w3.mode = kEpiF32;
+    w3.D = L.Gr + sh.oW3; w3.strideD = ps; w3.ldd = sh.H;
+    w3.err = &c->d_ctl->error;
+    CK(launch_gemm_bf16(w3, c->S, c->stream));
+    GemmParams g1 = g;  // dZ1 = (dZ2 W2) * [Z1 > 0]
+    g1.A = L.dZ2b; g1.strideA = rc * sh.H; g1.lda = sh.H;
+    g1.B = L.W2T; g1.strideB = (int64_t)sh.H * sh.H; g1.ldb = sh.H; g1.K = sh.H;
+    g1.gate = L.Z1; g1.D = L.dZ1; g1.H = nullptr; g1.HT = L.dZ1T;
+    CK(launch_gemm_bf16(g1, c->S, c->stream));
+    GemmParams w2 = w3;  // dW2 = dZ2^T H1
+    w2.A = L.dZ2T; w2.strideA = rc * sh.H; w2.B = L.H1T; w2.strideB = rc * sh.H;
+    w2.M = sh.H; w2.N = sh.H; w2.D = L.Gr + sh.oW2; w2.ldd = sh.H;
+    CK(launch_gemm_bf16(w2, c->S, c->stream));
+    GemmParams w1 = w3;  // dW1 = dZ1^T X
+    w1.A = L.dZ1T; w1.strideA = rc * sh.H; w1.B = L.XT; w1.strideB = rc * sh.Din;
+    w1.M = sh.H; w1.N = sh.Din; w1.D = L.Gr + sh.oW1; w1.ldd = sh.Din;
+    CK(launch_gemm_bf16(w1, c->S, c->stream));
+    CK(launch_colsum(L.dO, rows, sh.Dout, L.Gr + sh.ob3, nullptr, nullptr, c->S, rc * sh.Dout, ps, c->stream));
+    CK(launch_colsum(L.dZ2, rows, sh.H, L.Gr + sh.ob2, nullptr, nullptr, c->S, rc * sh.H, ps, c->stream));
+    CK(launch_colsum(L.dZ1, rows, sh.H, L.Gr + sh.ob1, L.Gr + sh.oC1, cond, c->S, rc * sh.H, ps, c->stream));
+    return PT_OK;
+}
+
+int learn_cast(pt_ctx *c) {
+    LearnState &L = *c->learn;
+    CastParams cp{};
+    cp.P = L.P; cp.M1 = L.M1; cp.M2 = L.M2; cp.M3 = L.M3;
+    cp.W1 = L.W1; cp.W2 = L.W2; cp.W3 = L.W3; cp.W2T = L.W2T; cp.W3T = L.W3T; cp.sh = L.sh;
+    CK(launch_cast(cp, c->stream));
+    return PT_OK;
+}
+
+DensityParams density_params(LearnState &L, const RawRows &raw, double *logq, int rows, bool grad) {
+    DensityParams d{};
+    d.O = L.O; d.raw = raw; d.rows_per_sample = rows; d.N = L.sh.N; d.Dout = L.sh.Dout; d.logq = logq;
+    d.inv_rows = 1.0f / (float)rows;
+    d.o_stride = L.rows;
+    if (grad) { d.dO = L.dO; d.dOb = L.dOb; d.dOT = L.dOT; d.lddt = L.rows; }
+    return d;
+}
+
+// One round of learned global moves on the chains at the ncold coldest temperatures of every sample.
+int run_global(pt_ctx *c) {
+    LearnState &L = *c->learn;
+    const ptgb::LearnShape &sh = L.sh;
+    const int np = L.nprop;
+    int rc;
+    CK(launch_cold_rows(c->d_perm, c->S, c->R, c->nT, sh.ncold, L.pslot, L.prow, L.pcond, c->stream));
+    // current configurations: features, density, exact FP64 energy
+    FeatParams fp{};
+    fp.a = c->d_a; fp.dbl = c->dbl ? 1 : 0; fp.samples = c->d_samples; fp.slot = L.pslot; fp.rows_per_sample = np;
+    fp.N = sh.N; fp.Din = sh.Din; fp.X = L.X; fp.XT = nullptr; fp.ldxt = L.rows; fp.raw = L.rcur;
+    fp.raw_stride = np; fp.raw_off = 0; fp.cond_in = nullptr; fp.x_stride = L.rows;
+    CK(launch_features(fp, c->S, c->stream));
+    if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
+    DensityParams dc = density_params(L, L.rcur, L.lq_cur, np, false);
+    CK(launch_density(dc, c->S, c->stream));
+    EnergyListParams ep{};
+    ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
+    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
+    CK(launch_energy_list(ep, c->S, c->stream));
+    // autoregressive sampling, one pass per block of modes
+    CK(cudaMemsetAsync(L.Xp, 0, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din, c->stream));
+    for (int b = 0; b < ptgb::kLearnBlocks; ++b) {
+        if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
+        SampleParams sp{};
+        sp.O = L.O; sp.rows_per_sample = np; sp.N = sh.N; sp.Dout = sh.Dout; sp.Din = sh.Din; sp.block = b;
+        sp.seed = c->seed; sp.row_id = L.prow; sp.ctl = c->d_ctl; sp.X = L.Xp; sp.u = L.rsamp.u; sp.phi = L.rsamp.phi;
+        sp.o_stride = L.rows; sp.x_stride = L.rows;
+        CK(launch_sample_block(sp, c->S, c->stream));
+    }
+    AssembleParams ap{};
+    ap.u = L.rsamp.u; ap.phi = L.rsamp.phi; ap.rows_per_sample = np; ap.N = sh.N; ap.seed = c->seed;
+    ap.row_id = L.prow; ap.ctl = c->d_ctl; ap.a = L.a_prop;
+    CK(launch_assemble(ap, c->S, c->stream));
+    // proposed configurations as stored: features, density, energy
+    FeatParams fq = fp;
+    fq.a = L.a_prop; fq.dbl = 1; fq.slot = nullptr; fq.raw = L.rprop;
+    CK(launch_features(fq, c->S, c->stream));
+    if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
+    DensityParams dq = density_params(L, L.rprop, L.lq_prop, np, false);
+    CK(launch_density(dq, c->S, c->stream));
+    EnergyListParams eq = ep;
+    eq.a = L.a_prop; eq.dbl = 1; eq.slot = nullptr; eq.E = L.H_prop;
+    CK(launch_energy_list(eq, c->S, c->stream));
+    MHParams mp{};
+    mp.logq_cur = L.lq_cur; mp.logq_prop = L.lq_prop; mp.H_cur = L.H_cur; mp.H_prop = L.H_prop;
+    mp.extra_cur = L.rcur.extra; mp.extra_prop = L.rprop.extra; mp.a_prop = L.a_prop; mp.a = c->d_a;
+    mp.dbl = c->dbl ? 1 : 0; mp.E = c->d_E; mp.slot = L.pslot; mp.samples = c->d_samples; mp.beta = c->d_beta;
+    mp.label = c->d_label; mp.rows_per_sample = np; mp.N = sh.N; mp.nT = c->nT; mp.seed = c->seed;
+    mp.row_id = L.prow; mp.ctl = c->d_ctl; mp.acc = c->d_gm_acc; mp.att = c->d_gm_att;
+    CK(launch_mh(mp, c->S, c->stream));
+    return PT_OK;
+}
+
+// One segment: seg sweeps, then resync / global moves / measure / swap as due at its end.
 int enqueue_segment(pt_ctx *c, const SegKey &k) {
     int rc;
     if ((rc = run_sweeps(c, k.seg)) != PT_OK) return rc;
     if (k.resync && (rc = run_energy(c, 1, nullptr, true)) != PT_OK) return rc;
+    if (k.global && (rc = run_global(c)) != PT_OK) return rc;
     if ((k.n_snap || k.live) && (rc = run_measure(c, k.n_snap, k.live)) != PT_OK) return rc;
     if (k.swap && (rc = run_swap(c)) != PT_OK) return rc;
-    CK(launch_advance(c->d_ctl, k.seg, k.swap ? 1 : 0, c->stream));
+    CK(launch_advance(c->d_ctl, k.seg, k.swap ? 1 : 0, k.global ? 1 : 0, c->stream));
     return PT_OK;
 }
 
@@ -575,6 +760,8 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
     RC(dalloc(c, &c->d_mc_att, c->n_chains));
     RC(dalloc(c, &c->d_mcT_acc, (size_t)S * n_T));
     RC(dalloc(c, &c->d_mcT_att, (size_t)S * n_T));
+    RC(dalloc(c, &c->d_gm_acc, (size_t)S * n_T));
+    RC(dalloc(c, &c->d_gm_att, (size_t)S * n_T));
     const size_t npair = (size_t)S * replicas * std::max(1, n_T - 1);
     RC(dalloc(c, &c->d_swap_acc, npair));
     RC(dalloc(c, &c->d_swap_att, npair));
@@ -595,7 +782,8 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
             else pack_sample<float>(lay[s], J + J_offsets[s], reinterpret_cast<float *>(hJ.data()) + c->samples[s].J_off * js);
         }
         CK(cudaMemcpy(c->d_J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
-    } else {
+    }
+    if (c->plain || c->maxN <= 64) {
         std::vector<int4> hq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<double> hJq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<int> hinc_off, hinc((size_t)std::max<int64_t>(inc_total, 1));
@@ -654,6 +842,8 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
     CK(cudaMemset(c->d_mc_att, 0, c->n_chains * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_mcT_acc, 0, (size_t)S * n_T * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_mcT_att, 0, (size_t)S * n_T * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_gm_acc, 0, (size_t)S * n_T * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_gm_att, 0, (size_t)S * n_T * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_swap_acc, 0, npair * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_swap_att, 0, npair * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_qhist, 0, (size_t)S * n_T * PT_QBINS * sizeof(unsigned long long)));
@@ -698,7 +888,8 @@ int pt_sweep(pt_ctx *c, int64_t n) {
     while (n > 0) {
         const int64_t d = c->sweeps_done;
         int64_t nb = d + c->max_seg;
-        for (int e : {cf.swap_every, cf.resync_every})
+        const int ge = c->learn ? c->learn->global_every : 0;
+        for (int e : {cf.swap_every, cf.resync_every, ge})
             if (e > 0) nb = std::min(nb, (d / e + 1) * e);
         const int seg = (int)std::min<int64_t>(n, nb - d);
         const int64_t end = d + seg;
@@ -712,6 +903,7 @@ int pt_sweep(pt_ctx *c, int64_t n) {
         }
         k.resync = (cf.resync_every > 0 && end % cf.resync_every == 0) ? 1 : 0;
         k.swap = (cf.swap_every > 0 && end % cf.swap_every == 0 && c->nT > 1) ? 1 : 0;
+        k.global = (ge > 0 && end % ge == 0) ? 1 : 0;
         if (k.n_snap > c->n_snap_max) return fail(c, PT_EINVAL, "pt_sweep: internal snapshot overflow");
         // a graph replays fixed sweep indices relative to the device counters: only the
         // segment shape enters the key
@@ -719,6 +911,7 @@ int pt_sweep(pt_ctx *c, int64_t n) {
         if (rc != PT_OK) return rc;
         c->sweeps_done = end;
         c->swap_passes += k.swap;
+        c->global_rounds += k.global;
         n -= seg;
     }
     return PT_OK;
@@ -729,7 +922,7 @@ int pt_swap(pt_ctx *c) {
     if (c->nT < 2) return PT_OK;
     const int rc = run_swap(c);
     if (rc != PT_OK) return rc;
-    CK(launch_advance(c->d_ctl, 0, 1, c->stream));
+    CK(launch_advance(c->d_ctl, 0, 1, 0, c->stream));
     c->swap_passes++;
     return PT_OK;
 }
@@ -754,6 +947,8 @@ int pt_measure(pt_ctx *c, pt_observables *o) {
     if (o->qhist) CK(cudaMemcpy(o->qhist, c->d_qhist, ST * PT_QBINS * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (o->swap_acc) CK(cudaMemcpy(o->swap_acc, c->d_swap_acc, npair * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (o->swap_att) CK(cudaMemcpy(o->swap_att, c->d_swap_att, npair * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (o->gm_acc) CK(cudaMemcpy(o->gm_acc, c->d_gm_acc, ST * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (o->gm_att) CK(cudaMemcpy(o->gm_att, c->d_gm_att, ST * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (o->mc_acc || o->mc_att) {
         std::vector<unsigned long long> ta(ST), tt(ST), ca(c->n_chains), ct(c->n_chains);
         std::vector<int> lab(c->n_chains);
@@ -785,6 +980,8 @@ int pt_reset_observables(pt_ctx *c) {
     CK(cudaMemsetAsync(c->d_mcT_att, 0, ST * sizeof(uint64_t), c->stream));
     CK(cudaMemsetAsync(c->d_mc_acc, 0, c->n_chains * sizeof(uint64_t), c->stream));
     CK(cudaMemsetAsync(c->d_mc_att, 0, c->n_chains * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_gm_acc, 0, ST * sizeof(uint64_t), c->stream));
+    CK(cudaMemsetAsync(c->d_gm_att, 0, ST * sizeof(uint64_t), c->stream));
     return PT_OK;
 }
 
@@ -901,7 +1098,7 @@ const char kMagic[8] = {'P', 'T', 'G', 'B', 'C', 'K', 'P', '1'};
 struct CkptHeader {
     char magic[8];
     int32_t version, S, R, nT, precision, n_chains;
-    int64_t a_total, sweeps_done, swap_passes;
+    int64_t a_total, sweeps_done, swap_passes, global_rounds;
     uint64_t seed, layout_hash;
 };
 uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -927,7 +1124,9 @@ std::vector<Blob> blobs(pt_ctx *c) {
             {c->d_qstat, ST * PT_NQSTAT * sizeof(double)},
             {c->d_qhist, ST * PT_QBINS * sizeof(uint64_t)},
             {c->d_swap_acc, npair * sizeof(uint64_t)},
-            {c->d_swap_att, npair * sizeof(uint64_t)}};
+            {c->d_swap_att, npair * sizeof(uint64_t)},
+            {c->d_gm_acc, ST * sizeof(uint64_t)},
+            {c->d_gm_att, ST * sizeof(uint64_t)}};
 }
 }  // namespace
 
@@ -945,6 +1144,7 @@ int pt_save(pt_ctx *c, void *buf, size_t *len) {
     std::memcpy(h.magic, kMagic, 8);
     h.version = 1; h.S = c->S; h.R = c->R; h.nT = c->nT; h.precision = c->cfg.precision; h.n_chains = c->n_chains;
     h.a_total = c->a_total; h.sweeps_done = c->sweeps_done; h.swap_passes = c->swap_passes; h.seed = c->seed;
+    h.global_rounds = c->global_rounds;
     h.layout_hash = layout_hash(c);
     std::memcpy(p, &h, sizeof(h));
     size_t off = sizeof(h);
@@ -984,9 +1184,11 @@ int pt_load(pt_ctx *c, const void *buf, size_t len) {
     Control ctl{};
     ctl.sweep_base = h.sweeps_done;
     ctl.swap_passes = h.swap_passes;
+    ctl.global_rounds = h.global_rounds;
     CK(cudaMemcpy(c->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
     c->sweeps_done = h.sweeps_done;
     c->swap_passes = h.swap_passes;
+    c->global_rounds = h.global_rounds;
     return PT_OK;
 }
 
@@ -1036,6 +1238,256 @@ int pt_autotune(pt_ctx *c, int trial_sweeps, int *chosen) {
     if (rc2 != PT_OK) return rc2;
     if (rc3 != PT_OK) return rc3;
     if (chosen) { chosen[0] = bestc.G; chosen[1] = bestc.ncw; chosen[2] = bestc.spu; }
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------------- learned proposal
+int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_t seed) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_learn_init: NULL context");
+    if (c->learn) return fail(c, PT_EINVAL, "pt_learn_init: already initialised");
+    const int N = c->N[0];
+    for (int n : c->N)
+        if (n != N) return fail(c, PT_EUNSUPPORTED, "pt_learn_init: the learned proposal needs one N for all samples");
+    if (N < 16 || N > 64 || N % 16) return fail(c, PT_EUNSUPPORTED, "pt_learn_init: the learned proposal supports N in {16, 32, 48, 64}");
+    if (n_cold < 1 || n_cold > c->nT || n_cold * c->R > 1024) return fail(c, PT_EINVAL, "pt_learn_init: need 1 <= n_cold <= n_T");
+    if (batch < 128 || batch % 128) return fail(c, PT_EINVAL, "pt_learn_init: batch must be a positive multiple of 128");
+    if (data_per_sample < batch) return fail(c, PT_EINVAL, "pt_learn_init: data_per_sample must be >= batch");
+    int rc = PT_OK;
+    LearnState *L = new LearnState();
+    c->learn = L;
+    ptgb::LearnShape &sh = L->sh;
+    sh.N = N; sh.H = 256; sh.Din = 3 * N; sh.Dout = 4 * N; sh.ncold = n_cold; sh.S = c->S;
+    sh.oW1 = 0;
+    sh.ob1 = sh.oW1 + (size_t)sh.H * sh.Din;
+    sh.oC1 = sh.ob1 + sh.H;
+    sh.oW2 = sh.oC1 + (size_t)n_cold * sh.H;
+    sh.ob2 = sh.oW2 + (size_t)sh.H * sh.H;
+    sh.oW3 = sh.ob2 + sh.H;
+    sh.ob3 = sh.oW3 + (size_t)sh.Dout * sh.H;
+    sh.psize = (sh.ob3 + sh.Dout + 63) / 64 * 64;
+    L->Mb = batch; L->ncap = data_per_sample; L->nprop = n_cold * c->R; L->seed = seed;
+    L->rows = std::max(batch, (L->nprop + 127) / 128 * 128);
+    const size_t S = c->S, ps = sh.psize, rows = L->rows;
+    L->P = lalloc<float>(c, S * ps, &rc); L->Gr = lalloc<float>(c, S * ps, &rc);
+    L->Am = lalloc<float>(c, S * ps, &rc); L->Av = lalloc<float>(c, S * ps, &rc);
+    L->M1 = lalloc<float>(c, (size_t)sh.H * sh.Din, &rc); L->M2 = lalloc<float>(c, (size_t)sh.H * sh.H, &rc);
+    L->M3 = lalloc<float>(c, (size_t)sh.Dout * sh.H, &rc);
+    L->W1 = lalloc<__nv_bfloat16>(c, S * sh.H * sh.Din, &rc); L->W2 = lalloc<__nv_bfloat16>(c, S * sh.H * sh.H, &rc);
+    L->W3 = lalloc<__nv_bfloat16>(c, S * sh.Dout * sh.H, &rc); L->W2T = lalloc<__nv_bfloat16>(c, S * sh.H * sh.H, &rc);
+    L->W3T = lalloc<__nv_bfloat16>(c, S * sh.Dout * sh.H, &rc);
+    L->du = lalloc<float>(c, S * L->ncap * N, &rc); L->dphi = lalloc<float>(c, S * L->ncap * N, &rc);
+    L->dextra = lalloc<float>(c, S * L->ncap, &rc); L->dcond = lalloc<int>(c, S * L->ncap, &rc);
+    L->X = lalloc<__nv_bfloat16>(c, S * rows * sh.Din, &rc); L->XT = lalloc<__nv_bfloat16>(c, S * rows * sh.Din, &rc);
+    L->Xp = lalloc<__nv_bfloat16>(c, S * rows * sh.Din, &rc);
+    L->H1 = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc); L->H1T = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc);
+    L->H2 = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc); L->H2T = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc);
+    L->Z1 = lalloc<float>(c, S * rows * sh.H, &rc); L->Z2 = lalloc<float>(c, S * rows * sh.H, &rc);
+    L->O = lalloc<float>(c, S * rows * sh.Dout, &rc); L->dO = lalloc<float>(c, S * rows * sh.Dout, &rc);
+    L->dOb = lalloc<__nv_bfloat16>(c, S * rows * sh.Dout, &rc); L->dOT = lalloc<__nv_bfloat16>(c, S * rows * sh.Dout, &rc);
+    L->dZ2 = lalloc<float>(c, S * rows * sh.H, &rc); L->dZ2b = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc);
+    L->dZ2T = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc); L->dZ1 = lalloc<float>(c, S * rows * sh.H, &rc);
+    L->dZ1T = lalloc<__nv_bfloat16>(c, S * rows * sh.H, &rc);
+    auto raw_rows = [&](RawRows &r, size_t n) {
+        r.u = lalloc<float>(c, n * N, &rc); r.phi = lalloc<float>(c, n * N, &rc);
+        r.extra = lalloc<float>(c, n, &rc); r.cond = lalloc<int>(c, n, &rc);
+    };
+    raw_rows(L->raw, S * rows);
+    raw_rows(L->rcur, S * L->nprop);
+    raw_rows(L->rprop, S * L->nprop);
+    raw_rows(L->rsamp, S * L->nprop);
+    L->logq = lalloc<double>(c, S * rows, &rc);
+    L->lq_cur = lalloc<double>(c, S * L->nprop, &rc); L->lq_prop = lalloc<double>(c, S * L->nprop, &rc);
+    L->H_cur = lalloc<double>(c, S * L->nprop, &rc); L->H_prop = lalloc<double>(c, S * L->nprop, &rc);
+    L->pslot = lalloc<int>(c, S * L->nprop, &rc); L->pcond = lalloc<int>(c, S * L->nprop, &rc);
+    L->prow = lalloc<uint32_t>(c, S * L->nprop, &rc);
+    L->a_prop = lalloc<double2>(c, S * L->nprop * N, &rc);
+    L->max_losses = 1 << 16;
+    L->losses = lalloc<double>(c, (size_t)L->max_losses, &rc);
+    if (rc != PT_OK) return rc;
+    // block-autoregressive masks: input features of mode k have degree blk(k) + 1, hidden unit h degree h % 8,
+    // output k depends on hidden units of degree <= blk(k)
+    const int per = N / ptgb::kLearnBlocks;
+    std::vector<float> m1((size_t)sh.H * sh.Din), m2((size_t)sh.H * sh.H), m3((size_t)sh.Dout * sh.H);
+    for (int h = 0; h < sh.H; ++h)
+        for (int i = 0; i < sh.Din; ++i) m1[(size_t)h * sh.Din + i] = ((i / 3) / per + 1 <= h % ptgb::kLearnBlocks) ? 1.f : 0.f;
+    for (int h2 = 0; h2 < sh.H; ++h2)
+        for (int h1 = 0; h1 < sh.H; ++h1) m2[(size_t)h2 * sh.H + h1] = (h1 % ptgb::kLearnBlocks <= h2 % ptgb::kLearnBlocks) ? 1.f : 0.f;
+    for (int o = 0; o < sh.Dout; ++o)
+        for (int h = 0; h < sh.H; ++h) m3[(size_t)o * sh.H + h] = (h % ptgb::kLearnBlocks <= (o / 4) / per) ? 1.f : 0.f;
+    // initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)), output layer scaled by 0.1, biases 0
+    std::vector<float> hp(S * ps, 0.f);
+    uint64_t st = seed ^ 0x9E3779B97F4A7C15ull;
+    auto urand = [&]() {  // splitmix64
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t s = 0; s < S; ++s) {
+        float *P = hp.data() + s * ps;
+        const double a1 = 1.0 / std::sqrt((double)sh.Din), a2 = 1.0 / std::sqrt((double)sh.H);
+        for (size_t i = 0; i < (size_t)sh.H * sh.Din; ++i) P[sh.oW1 + i] = (float)((2 * urand() - 1) * a1);
+        for (size_t i = 0; i < (size_t)sh.H * sh.H; ++i) P[sh.oW2 + i] = (float)((2 * urand() - 1) * a2);
+        for (size_t i = 0; i < (size_t)sh.Dout * sh.H; ++i) P[sh.oW3 + i] = (float)((2 * urand() - 1) * a2 * 0.1);
+    }
+    CK(cudaMemcpy(L->P, hp.data(), hp.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L->M1, m1.data(), m1.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L->M2, m2.data(), m2.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L->M3, m3.data(), m3.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemset(L->Am, 0, S * ps * sizeof(float)));
+    CK(cudaMemset(L->Av, 0, S * ps * sizeof(float)));
+    if ((rc = learn_cast(c)) != PT_OK) return rc;
+    return watchdog_sync(c);
+}
+
+int pt_learn_params(pt_ctx *c, float *P, int set) {
+    if (!c || !P) return fail(c, PT_EINVAL, "pt_learn_params: NULL argument");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_learn_params: call pt_learn_init first");
+    LearnState &L = *c->learn;
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    const size_t n = (size_t)c->S * L.sh.psize;
+    if (set) {
+        CK(cudaMemcpy(L.P, P, n * sizeof(float), cudaMemcpyHostToDevice));
+        if ((rc = learn_cast(c)) != PT_OK) return rc;
+        return watchdog_sync(c);
+    }
+    CK(cudaMemcpy(P, L.P, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+int pt_learn_shape(pt_ctx *c, int64_t *out) {
+    if (!c || !out) return fail(c, PT_EINVAL, "pt_learn_shape: NULL argument");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_learn_shape: call pt_learn_init first");
+    const ptgb::LearnShape &sh = c->learn->sh;
+    const int64_t v[12] = {sh.N, sh.H, sh.Din, sh.Dout, sh.ncold, (int64_t)sh.psize, (int64_t)sh.oW1, (int64_t)sh.ob1,
+                           (int64_t)sh.oC1, (int64_t)sh.oW2, (int64_t)sh.ob2, (int64_t)sh.oW3};
+    for (int i = 0; i < 12; ++i) out[i] = v[i];
+    out[12] = (int64_t)sh.ob3;
+    out[13] = c->learn->ndata;
+    return PT_OK;
+}
+
+int pt_learn_eval(pt_ctx *c, const double *a, const int *cond, int rows, double *logq, double *extra, float *grad) {
+    if (!c || !a || !cond || !logq) return fail(c, PT_EINVAL, "pt_learn_eval: NULL argument");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_learn_eval: call pt_learn_init first");
+    LearnState &L = *c->learn;
+    const ptgb::LearnShape &sh = L.sh;
+    if (rows < 1 || rows > L.rows || (grad && rows % 8)) return fail(c, PT_EINVAL, "pt_learn_eval: bad row count");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    const size_t S = c->S, N = sh.N;
+    std::vector<int> hc(S * rows);
+    for (size_t i = 0; i < hc.size(); ++i) {
+        if (cond[i] < 0 || cond[i] >= sh.ncold) return fail(c, PT_EINVAL, "pt_learn_eval: condition out of range");
+        hc[i] = cond[i];
+    }
+    const size_t na = S * rows * N;
+    double2 *da = nullptr;
+    int *dc = nullptr;
+    CK(cudaMalloc(&da, na * sizeof(double2)));
+    cudaError_t e = cudaMalloc(&dc, hc.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(da, a, na * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(da); cudaFree(dc); return cuda_fail(c, e, "pt_learn_eval upload"); }
+    FeatParams fp{};
+    fp.a = da; fp.dbl = 1; fp.samples = c->d_samples; fp.slot = nullptr; fp.rows_per_sample = rows; fp.N = sh.N;
+    fp.Din = sh.Din; fp.X = L.X; fp.XT = grad ? L.XT : nullptr; fp.ldxt = L.rows; fp.raw = L.raw;
+    fp.raw_stride = rows; fp.raw_off = 0; fp.cond_in = dc; fp.x_stride = L.rows;
+    e = launch_features(fp, c->S, c->stream);
+    if (e == cudaSuccess) {
+        rc = learn_forward(c, L.X, rows, L.raw.cond, rows, grad != nullptr);
+        if (rc == PT_OK) {
+            DensityParams d = density_params(L, L.raw, L.logq, rows, grad != nullptr);
+            e = launch_density(d, c->S, c->stream);
+            if (e == cudaSuccess && grad) rc = learn_backward(c, rows, L.raw.cond);
+        }
+    }
+    if (e == cudaSuccess && rc == PT_OK) e = cudaStreamSynchronize(c->stream);
+    cudaFree(da);
+    cudaFree(dc);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pt_learn_eval");
+    if (rc != PT_OK) return rc;
+    CK(cudaMemcpy(logq, L.logq, S * rows * sizeof(double), cudaMemcpyDeviceToHost));
+    if (extra) {
+        std::vector<float> hx(S * rows);
+        CK(cudaMemcpy(hx.data(), L.raw.extra, hx.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < hx.size(); ++i) extra[i] = hx[i];
+    }
+    if (grad) CK(cudaMemcpy(grad, L.Gr, S * sh.psize * sizeof(float), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+int pt_collect(pt_ctx *c, int64_t every, int rounds) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_collect: NULL context");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_collect: call pt_learn_init first");
+    if (every < 0 || rounds < 0) return fail(c, PT_EINVAL, "pt_collect: negative argument");
+    LearnState &L = *c->learn;
+    int rc;
+    for (int r = 0; r < rounds; ++r) {
+        if (L.ndata + L.nprop > L.ncap) break;
+        if (every > 0 && (rc = pt_sweep(c, every)) != PT_OK) return rc;
+        CK(launch_cold_rows(c->d_perm, c->S, c->R, c->nT, L.sh.ncold, L.pslot, L.prow, L.pcond, c->stream));
+        FeatParams fp{};
+        fp.a = c->d_a; fp.dbl = c->dbl ? 1 : 0; fp.samples = c->d_samples; fp.slot = L.pslot;
+        fp.rows_per_sample = L.nprop; fp.N = L.sh.N; fp.Din = L.sh.Din; fp.X = nullptr; fp.XT = nullptr;
+        fp.raw.u = L.du; fp.raw.phi = L.dphi; fp.raw.extra = L.dextra; fp.raw.cond = L.dcond;
+        fp.raw_stride = L.ncap; fp.raw_off = L.ndata; fp.cond_in = L.pcond; fp.x_stride = L.rows;
+        CK(launch_features(fp, c->S, c->stream));
+        L.ndata += L.nprop;
+    }
+    return PT_OK;
+}
+
+int pt_train(pt_ctx *c, int steps, double lr, double *losses) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_train: NULL context");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_train: call pt_learn_init first");
+    LearnState &L = *c->learn;
+    if (L.ndata < 1) return fail(c, PT_EINVAL, "pt_train: no training configurations (pt_collect)");
+    if (steps < 0 || steps > L.max_losses || !(lr > 0.0)) return fail(c, PT_EINVAL, "pt_train: bad steps or lr");
+    const ptgb::LearnShape &sh = L.sh;
+    int rc;
+    for (int t = 0; t < steps; ++t) {
+        GatherParams gp{};
+        gp.du = L.du; gp.dphi = L.dphi; gp.dextra = L.dextra; gp.dcond = L.dcond;
+        gp.ndata = L.ndata; gp.stride = L.ncap;  // rows of sample s live at s * ncap, ndata of them collected
+        gp.rows = L.Mb; gp.N = sh.N; gp.Din = sh.Din; gp.ldxt = L.rows; gp.seed = L.seed; gp.step = L.step++;
+        gp.X = L.X; gp.XT = L.XT; gp.raw = L.raw; gp.x_stride = L.rows;
+        CK(launch_gather(gp, c->S, c->stream));
+        if ((rc = learn_forward(c, L.X, L.Mb, L.raw.cond, L.Mb, true)) != PT_OK) return rc;
+        DensityParams d = density_params(L, L.raw, L.logq, L.Mb, true);
+        CK(launch_density(d, c->S, c->stream));
+        if ((rc = learn_backward(c, L.Mb, L.raw.cond)) != PT_OK) return rc;
+        CK(launch_adam(L.P, L.Gr, L.Am, L.Av, (size_t)c->S * sh.psize, (float)lr, 0.9f, 0.999f, 1e-8f, ++L.adam_t,
+                       c->stream));
+        if ((rc = learn_cast(c)) != PT_OK) return rc;
+        if (losses) {
+            // mean over samples and rows of -(log q + extra): the NLL on the constraint surface
+            CK(launch_learn_loss(L.logq, L.raw.extra, c->S, L.Mb, L.losses + t, c->stream));
+        }
+    }
+    if ((rc = watchdog_sync(c)) != PT_OK) return rc;
+    if (losses && steps > 0) CK(cudaMemcpy(losses, L.losses, steps * sizeof(double), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+int pt_global_move(pt_ctx *c) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_global_move: NULL context");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_global_move: call pt_learn_init first");
+    const int rc = run_global(c);
+    if (rc != PT_OK) return rc;
+    CK(launch_advance(c->d_ctl, 0, 0, 1, c->stream));
+    c->global_rounds++;
+    return PT_OK;
+}
+
+int pt_set_global_every(pt_ctx *c, int every) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_set_global_every: NULL context");
+    if (every < 0) return fail(c, PT_EINVAL, "pt_set_global_every: negative interval");
+    if (every > 0 && !c->learn) return fail(c, PT_EINVAL, "pt_set_global_every: call pt_learn_init first");
+    if (c->learn) c->learn->global_every = every;
     return PT_OK;
 }
 

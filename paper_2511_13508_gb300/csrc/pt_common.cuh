@@ -112,6 +112,7 @@ struct Control {
     int pad_;
     long long sweep_base;   // sweeps done before the current sweep launch
     long long swap_passes;  // swap passes done
+    long long global_rounds;  // learned global-move rounds done
 };
 
 constexpr int kErrTimeout = 1, kErrNaN = 2, kErrBadArg = 3;

@@ -147,6 +147,6 @@ struct PlainParams {
 cudaError_t launch_plain_sweep(const PlainParams &p, int n_chains, cudaStream_t s);
 cudaError_t launch_plain_energy(const PlainParams &p, int n_chains, cudaStream_t s);
 
-cudaError_t launch_advance(Control *ctl, long long sweeps, long long swap_passes, cudaStream_t s);
+cudaError_t launch_advance(Control *ctl, long long sweeps, long long swap_passes, long long rounds, cudaStream_t s);
 
 }  // namespace ptgb

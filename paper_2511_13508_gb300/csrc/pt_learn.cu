@@ -1,0 +1,481 @@
+// pt_learn.cu -- kernels of the learned global-move proposal: gauge-fixed features, the proposal
+// density and its gradient with respect to the network outputs, bias gradients, Adam, block-wise
+// sampling, assembly of proposed configurations, FP64 energies and the exact Metropolis-Hastings step.
+// The dense layers run on the tensor cores (pt_gemm.cu).  See pt_learn.h for the density.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include "pt_common.cuh"
+#include "pt_learn.h"
+
+namespace ptgb {
+
+namespace {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr float kLog2PiHalf = 0.91893853320467274178f;  // log(2 pi) / 2
+constexpr float kRhoMax = 0.98f;
+constexpr float kUScale = 0.25f;                          // input scale of logit(v)
+
+__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float wrap2pi(float x) { return x - kTwoPiF * floorf(x / kTwoPiF); }
+
+// Input features of mode k: (logit(v_k)/4 clipped to [-4, 4], cos phi~_k, sin phi~_k).
+__device__ __forceinline__ void feature_triplet(float u, float ph, int k, int N, float f[3]) {
+    f[0] = (k <= N - 2) ? fminf(fmaxf(u * kUScale, -4.f), 4.f) : 0.f;
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    f[1] = cs;
+    f[2] = sn;
+}
+
+__device__ __forceinline__ double warp_sumd(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// gauge-fixed features of configurations: one warp per row, N <= 64 (two modes per lane)
+__global__ void features_kernel(FeatParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= p.rows_per_sample) return;
+    const int N = p.N;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    double re[2] = {0, 0}, im[2] = {0, 0};
+    if (p.slot) {
+        const int slot = p.slot[grow];
+        const SampleDev sd = p.samples[s];
+        const int64_t base = sd.a_off + (int64_t)(slot - sd.chain0) * N;
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            if (k < N) {
+                if (p.dbl) { const double2 v = reinterpret_cast<const double2 *>(p.a)[base + k]; re[q] = v.x; im[q] = v.y; }
+                else { const float2 v = reinterpret_cast<const float2 *>(p.a)[base + k]; re[q] = v.x; im[q] = v.y; }
+            }
+        }
+    } else {
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            if (k < N) {
+                if (p.dbl) { const double2 v = reinterpret_cast<const double2 *>(p.a)[grow * N + k]; re[q] = v.x; im[q] = v.y; }
+                else { const float2 v = reinterpret_cast<const float2 *>(p.a)[grow * N + k]; re[q] = v.x; im[q] = v.y; }
+            }
+        }
+    }
+    // intensity fractions s_k = |a_k|^4 / sum |a|^4 (exactly on the simplex)
+    double sk[2], tot = 0.0;
+    for (int q = 0; q < 2; ++q) {
+        const double u = re[q] * re[q] + im[q] * im[q];
+        sk[q] = (lane + 32 * q < N) ? u * u : 0.0;
+        tot += sk[q];
+    }
+    tot = warp_sumd(tot);
+    for (int q = 0; q < 2; ++q) sk[q] /= tot;
+    // suffix sums R_k = sum_{i >= k} s_i and R_{k+1}, summed from the tail (no cancellation: a proposal's
+    // intensities can fall off geometrically, and 1 - prefix would lose the tail entirely)
+    double Rin[2], Rex[2];
+    {
+        double x0 = sk[0], x1 = sk[1];
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y0 = __shfl_down_sync(0xffffffffu, x0, o), y1 = __shfl_down_sync(0xffffffffu, x1, o);
+            if (lane + o < 32) { x0 += y0; x1 += y1; }
+        }
+        const double top = __shfl_sync(0xffffffffu, x1, 0);  // sum over modes 32..63
+        const double n0 = __shfl_down_sync(0xffffffffu, x0, 1), n1 = __shfl_down_sync(0xffffffffu, x1, 1);
+        Rin[0] = x0 + top;
+        Rin[1] = x1;
+        Rex[0] = (lane < 31 ? n0 : 0.0) + top;
+        Rex[1] = lane < 31 ? n1 : 0.0;
+    }
+    // phases, gauge fixed
+    const double ph0 = __shfl_sync(0xffffffffu, atan2(im[0], re[0]), 0);
+    const double ph1 = __shfl_sync(0xffffffffu, atan2(im[0], re[0]), 1);
+    double extra = 0.0;
+    const int64_t rrow = (int64_t)s * p.raw_stride + p.raw_off + row;
+    for (int q = 0; q < 2; ++q) {
+        const int k = lane + 32 * q;
+        if (k >= N) continue;
+        const double Rk = Rin[q], Rk1 = Rex[q];
+        const float u = (k <= N - 2) ? (float)(log(sk[q]) - log(fmax(Rk1, 1e-300))) : 0.f;
+        float ph = 0.f;
+        if (k >= 2) ph = wrap2pi((float)(atan2(im[q], re[q]) - ph0 - (double)k * (ph1 - ph0)));
+        if (k <= N - 2) extra -= log(fmax(Rk, 1e-300));
+        extra += 0.5 * log(sk[q]);
+        p.raw.u[rrow * N + k] = u;
+        p.raw.phi[rrow * N + k] = ph;
+        if (p.X) {
+            float f[3];
+            feature_triplet(u, ph, k, N, f);
+            for (int c = 0; c < 3; ++c) {
+                const int fi = 3 * k + c;
+                const __nv_bfloat16 b = __float2bfloat16_rn(f[c]);
+                p.X[((int64_t)s * p.x_stride + row) * p.Din + fi] = b;
+                if (p.XT) p.XT[((int64_t)s * p.Din + fi) * p.ldxt + row] = b;
+            }
+        }
+    }
+    extra = warp_sumd(extra);
+    if (lane == 0) {
+        p.raw.extra[rrow] = (float)extra;
+        if (p.cond_in) p.raw.cond[rrow] = p.cond_in[grow];
+    }
+}
+
+cudaError_t launch_features(const FeatParams &p, int S, cudaStream_t s) {
+    if (p.rows_per_sample <= 0) return cudaSuccess;
+    dim3 grid((p.rows_per_sample + 3) / 4, S);
+    features_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void cast_kernel(CastParams p) {
+    const LearnShape &sh = p.sh;
+    const int s = blockIdx.y;
+    const float *P = p.P + (size_t)s * sh.psize;
+    const size_t n1 = (size_t)sh.H * sh.Din, n2 = (size_t)sh.H * sh.H, n3 = (size_t)sh.Dout * sh.H;
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3; i += gridDim.x * blockDim.x) {
+        if (i < n1) {
+            p.W1[s * n1 + i] = __float2bfloat16_rn(P[sh.oW1 + i] * p.M1[i]);
+        } else if (i < n1 + n2) {
+            const size_t j = i - n1;
+            const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW2 + j] * p.M2[j]);
+            p.W2[s * n2 + j] = w;
+            const size_t h2 = j / sh.H, h1 = j % sh.H;
+            p.W2T[s * n2 + h1 * sh.H + h2] = w;
+        } else {
+            const size_t j = i - n1 - n2;
+            const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW3 + j] * p.M3[j]);
+            p.W3[s * n3 + j] = w;
+            const size_t o = j / sh.H, h = j % sh.H;
+            p.W3T[s * n3 + h * sh.Dout + o] = w;
+        }
+    }
+}
+
+cudaError_t launch_cast(const CastParams &p, cudaStream_t s) {
+    dim3 grid(128, p.sh.S);
+    cast_kernel<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// log q per row and the gradient of mean(-log q) with respect to the outputs (mu, log sigma, m, rho_raw)
+__global__ void density_kernel(DensityParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= p.rows_per_sample) return;
+    const int N = p.N;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    const int64_t orow = (int64_t)s * p.o_stride + row;
+    const float *o = p.O + orow * p.Dout;
+    double lq = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        if (k <= N - 2) {
+            const float u = p.raw.u[grow * N + k];
+            const float mu = o[4 * k], ls_raw = o[4 * k + 1];
+            const float ls = fminf(fmaxf(ls_raw, -7.f), 3.f);
+            const float sig = expf(ls);
+            const float z = (u - mu) / sig;
+            lq += (double)(-0.5f * z * z - ls - kLog2PiHalf + softplusf(-u) + softplusf(u));
+            g[0] = z / sig;
+            g[1] = (ls_raw > -7.f && ls_raw < 3.f) ? (z * z - 1.f) : 0.f;
+        }
+        if (k >= 2) {
+            const float ph = p.raw.phi[grow * N + k];
+            const float m = o[4 * k + 2], rr = o[4 * k + 3];
+            const float sg = 1.f / (1.f + expf(-rr));
+            const float rho = kRhoMax * sg;
+            float sd, cd;
+            sincosf(ph - m, &sd, &cd);
+            const float D = 1.f + rho * rho - 2.f * rho * cd;
+            lq += (double)(log1pf(-rho * rho) - 2.f * kLog2PiHalf - logf(D));
+            g[2] = 2.f * rho * sd / D;
+            const float dl_drho = -2.f * rho / (1.f - rho * rho) - (2.f * rho - 2.f * cd) / D;
+            g[3] = dl_drho * kRhoMax * sg * (1.f - sg);
+        }
+        if (p.dO || p.dOb) {
+            for (int c = 0; c < 4; ++c) {
+                const float d = -g[c] * p.inv_rows;  // d mean(-log q) / d output
+                const int col = 4 * k + c;
+                if (p.dO) p.dO[orow * p.Dout + col] = d;
+                const __nv_bfloat16 b = __float2bfloat16_rn(d);
+                if (p.dOb) p.dOb[orow * p.Dout + col] = b;
+                if (p.dOT) p.dOT[((int64_t)s * p.Dout + col) * p.lddt + row] = b;
+            }
+        }
+    }
+    lq = warp_sumd(lq);
+    if (lane == 0) p.logq[grow] = lq;
+}
+
+cudaError_t launch_density(const DensityParams &p, int S, cudaStream_t s) {
+    if (p.rows_per_sample <= 0) return cudaSuccess;
+    dim3 grid((p.rows_per_sample + 3) / 4, S);
+    density_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void colsum_kernel(const float *dZ, int rows, int cols, float *db, float *dC, const int *cond,
+                              int64_t strideZ, int64_t strideGrad, int64_t strideCond) {
+    const int s = blockIdx.y, col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= cols) return;
+    const float *z = dZ + s * strideZ;
+    float acc = 0.f;
+    for (int r = 0; r < rows; ++r) {
+        const float v = z[(int64_t)r * cols + col];
+        acc += v;
+        if (dC) dC[s * strideGrad + (int64_t)cond[s * strideCond + r] * cols + col] += v;
+    }
+    db[s * strideGrad + col] = acc;
+}
+
+cudaError_t launch_colsum(const float *dZ, int rows, int cols, float *db, float *dC, const int *cond, int S,
+                          int64_t strideZ, int64_t strideGrad, cudaStream_t s) {
+    dim3 grid((cols + 127) / 128, S);
+    colsum_kernel<<<grid, 128, 0, s>>>(dZ, rows, cols, db, dC, cond, strideZ, strideGrad, rows);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void adam_kernel(float *P, const float *G, float *m, float *v, size_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g, vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+cudaError_t launch_adam(float *P, const float *G, float *m, float *v, size_t n, float lr, float b1, float b2,
+                        float eps, int t, cudaStream_t s) {
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<512, 256, 0, s>>>(P, G, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void gather_kernel(GatherParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= p.rows) return;
+    const int N = p.N;
+    const u32x4 w = draw(p.seed, (uint32_t)s, p.step, (uint32_t)row, kTagBatch);
+    const int idx = (int)(((uint64_t)w.x * (uint64_t)p.ndata) >> 32);
+    const int64_t src = (int64_t)s * p.stride + idx, dst = (int64_t)s * p.rows + row;
+    const int64_t xrow = (int64_t)s * p.x_stride + row;
+    for (int k = lane; k < N; k += 32) {
+        const float u = p.du[src * N + k], ph = p.dphi[src * N + k];
+        p.raw.u[dst * N + k] = u;
+        p.raw.phi[dst * N + k] = ph;
+        float f[3];
+        feature_triplet(u, ph, k, N, f);
+        for (int c = 0; c < 3; ++c) {
+            const int fi = 3 * k + c;
+            const __nv_bfloat16 b = __float2bfloat16_rn(f[c]);
+            p.X[xrow * p.Din + fi] = b;
+            p.XT[((int64_t)s * p.Din + fi) * p.ldxt + row] = b;
+        }
+    }
+    if (lane == 0) {
+        p.raw.extra[dst] = p.dextra[src];
+        p.raw.cond[dst] = p.dcond[src];
+    }
+}
+
+cudaError_t launch_gather(const GatherParams &p, int S, cudaStream_t s) {
+    dim3 grid((p.rows + 3) / 4, S);
+    gather_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// sampling pass for mode block b: u = mu + sigma * eps (Box-Muller), phi~ by the wrapped-Cauchy inverse CDF
+__global__ void sample_block_kernel(SampleParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= p.rows_per_sample) return;
+    const int N = p.N, per = N / kLearnBlocks;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    const uint32_t id = p.row_id[grow];
+    for (int t = lane; t < per; t += 32) {
+        const int k = p.block * per + t;
+        const float *o = p.O + ((int64_t)s * p.o_stride + row) * p.Dout + 4 * k;
+        const u32x4 w = draw(p.seed, id, (uint32_t)p.ctl->global_rounds, (uint32_t)k, kTagGlobal);
+        float u = 0.f, ph = 0.f;
+        if (k <= N - 2) {
+            const float ls = fminf(fmaxf(o[1], -7.f), 3.f);
+            const float eps = (float)(sqrt(-2.0 * log(u01(w.x))) * cos(kTwoPi * u01(w.y)));
+            u = o[0] + expf(ls) * eps;
+        }
+        if (k >= 2) {
+            const float rho = kRhoMax / (1.f + expf(-o[3]));
+            const float t1 = tanf(3.14159265358979323846f * ((float)u01(w.z) - 0.5f));
+            ph = wrap2pi(o[2] + 2.f * atanf((1.f - rho) / (1.f + rho) * t1));
+        }
+        p.u[grow * N + k] = u;
+        p.phi[grow * N + k] = ph;
+        float f[3];
+        feature_triplet(u, ph, k, N, f);
+        for (int c = 0; c < 3; ++c) p.X[((int64_t)s * p.x_stride + row) * p.Din + 3 * k + c] = __float2bfloat16_rn(f[c]);
+    }
+}
+
+cudaError_t launch_sample_block(const SampleParams &p, int S, cudaStream_t s) {
+    dim3 grid((p.rows_per_sample + 3) / 4, S);
+    sample_block_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// amplitudes: v_k = sigmoid(u_k), s_k = v_k r_k (stick breaking), |a_k| = (N s_k)^(1/4),
+// phi_k = phi~_k + alpha + k theta with a fresh uniform gauge (alpha, theta)
+__global__ void assemble_kernel(AssembleParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= p.rows_per_sample) return;
+    const int N = p.N;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    const u32x4 w = draw(p.seed, p.row_id[grow], (uint32_t)p.ctl->global_rounds, (uint32_t)N, kTagGlobal);
+    const double alpha = kTwoPi * u01(w.x), theta = kTwoPi * u01(w.y);
+    double r = 1.0;
+    for (int k = 0; k < N; ++k) {
+        double sk;
+        if (k <= N - 2) {
+            const double u = p.u[grow * N + k];
+            sk = r / (1.0 + exp(-u));  // v_k r_k
+            r = r / (1.0 + exp(u));    // r_{k+1} = r_k (1 - v_k), without cancellation
+        } else {
+            sk = r;
+        }
+        const double A = sqrt(sqrt((double)N * fmax(sk, 0.0)));
+        const double ph = (double)p.phi[grow * N + k] + alpha + (double)k * theta;
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        p.a[grow * N + k] = make_double2(A * cs, A * sn);
+    }
+}
+
+cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
+    dim3 grid((p.rows_per_sample + 63) / 64, S);
+    assemble_kernel<<<grid, 64, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void energy_list_kernel(EnergyListParams p) {
+    __shared__ double2 sa[512];
+    __shared__ double red[32];
+    const int s = blockIdx.y, row = blockIdx.x, N = p.N;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    const SampleDev sd = p.samples[s];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        if (p.slot) {
+            const int64_t base = sd.a_off + (int64_t)(p.slot[grow] - sd.chain0) * N;
+            if (p.dbl) sa[k] = reinterpret_cast<const double2 *>(p.a)[base + k];
+            else { const float2 v = reinterpret_cast<const float2 *>(p.a)[base + k]; sa[k] = make_double2(v.x, v.y); }
+        } else if (p.dbl) {
+            sa[k] = reinterpret_cast<const double2 *>(p.a)[grow * N + k];
+        } else {
+            const float2 v = reinterpret_cast<const float2 *>(p.a)[grow * N + k];
+            sa[k] = make_double2(v.x, v.y);
+        }
+    }
+    __syncthreads();
+    const int4 *Q = p.quads + sd.q_off;
+    const double *J = p.Jq + sd.q_off;
+    double acc = 0.0;
+    for (int64_t q = threadIdx.x; q < sd.nq; q += blockDim.x) {
+        const int4 t = Q[q];
+        const double2 a = sa[t.x], b = sa[t.y], c = sa[t.z], d = sa[t.w];
+        // Re( conj(a) b c conj(d) )
+        const double xr = a.x * b.x + a.y * b.y, xi = a.x * b.y - a.y * b.x;   // conj(a) b
+        const double yr = c.x * d.x + c.y * d.y, yi = c.y * d.x - c.x * d.y;   // c conj(d)
+        acc += J[q] * (xr * yr - xi * yi);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        p.E[grow] = -p.cc * t;
+    }
+}
+
+cudaError_t launch_energy_list(const EnergyListParams &p, int S, cudaStream_t s) {
+    if (p.rows_per_sample <= 0) return cudaSuccess;
+    dim3 grid(p.rows_per_sample, S);
+    energy_list_kernel<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+__global__ void mh_kernel(MHParams p) {
+    const int s = blockIdx.y, row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= p.rows_per_sample) return;
+    const int64_t grow = (int64_t)s * p.rows_per_sample + row;
+    const int slot = p.slot[grow];
+    const int t = p.label[slot];
+    const double beta = p.beta[t];
+    const double lA = -beta * (p.H_prop[grow] - p.H_cur[grow]) + (p.logq_cur[grow] + (double)p.extra_cur[grow]) -
+                      (p.logq_prop[grow] + (double)p.extra_prop[grow]);
+    const u32x4 w = draw(p.seed, p.row_id[grow], (uint32_t)p.ctl->global_rounds, (uint32_t)(p.N + 1), kTagGlobal);
+    const bool acc = isfinite(lA) && (lA >= 0.0 || log(u01(w.x)) < lA);
+    atomicAdd(p.att + (int64_t)s * p.nT + t, 1ull);
+    if (acc) {
+        atomicAdd(p.acc + (int64_t)s * p.nT + t, 1ull);
+        const SampleDev sd = p.samples[s];
+        const int64_t base = sd.a_off + (int64_t)(slot - sd.chain0) * p.N;
+        for (int k = 0; k < p.N; ++k) {
+            const double2 v = p.a_prop[grow * p.N + k];
+            if (p.dbl) reinterpret_cast<double2 *>(p.a)[base + k] = v;
+            else reinterpret_cast<float2 *>(p.a)[base + k] = make_float2((float)v.x, (float)v.y);
+        }
+        p.E[slot] = p.H_prop[grow];
+    }
+}
+
+cudaError_t launch_mh(const MHParams &p, int S, cudaStream_t s) {
+    dim3 grid((p.rows_per_sample + 63) / 64, S);
+    mh_kernel<<<grid, 64, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+__global__ void learn_loss_kernel(const double *logq, const float *extra, int n, double *out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc -= logq[i] + (double)extra[i];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        *out = t / n;
+    }
+}
+
+cudaError_t launch_learn_loss(const double *logq, const float *extra, int S, int rows, double *out, cudaStream_t s) {
+    learn_loss_kernel<<<1, 256, 0, s>>>(logq, extra, S * rows, out);
+    return cudaGetLastError();
+}
+
+__global__ void cold_rows_kernel(const int *perm, int S, int R, int nT, int ncold, int *slot, uint32_t *row_id,
+                                 int *cond) {
+    const int s = blockIdx.x, i = threadIdx.x;
+    if (i >= ncold * R) return;
+    const int t = i / R, r = i % R;
+    const int64_t out = (int64_t)s * ncold * R + i;
+    slot[out] = perm[((int64_t)s * R + r) * nT + t];
+    row_id[out] = (uint32_t)((s * R + r) * nT + t);
+    cond[out] = t;
+}
+
+cudaError_t launch_cold_rows(const int *perm, int S, int R, int nT, int ncold, int *slot, uint32_t *row_id,
+                             int *cond, cudaStream_t s) {
+    cold_rows_kernel<<<S, 1024, 0, s>>>(perm, S, R, nT, ncold, slot, row_id, cond);
+    return cudaGetLastError();
+}
+
+}  // namespace ptgb

@@ -1,6 +1,7 @@
 """Learned global-move proposal: tensor-core GEMM, network forward/backward and the exact MH move,
 through the C ABI, against plain FP32/FP64 references."""
 import ctypes
+import math
 
 import numpy as np
 import pytest
@@ -35,3 +36,240 @@ def test_tcgen05_gemm_matches_fp32_reference(batch, M, N, K):
     ref = torch.bmm(A.float(), B.float().transpose(1, 2))
     err = (D - ref).abs().max().item()
     assert err <= 1e-4 * ref.abs().max().item() + 1e-4, err
+
+
+# ------------------------------------------------------------------------------ learned proposal
+from oracle import learned as ol  # noqa: E402
+from paper_2511_13508_gb300 import workload  # noqa: E402
+
+
+def _couplings(Ns, seed0=2000):
+    import oracle
+    return [workload.couplings(N, len(oracle.enumerate_quads(N)), seed0 + s) for s, N in enumerate(Ns)]
+
+
+def _dirichlet(N, shape, alpha, rng):
+    g = rng.gamma(alpha, size=shape + (N,))
+    s = g / g.sum(-1, keepdims=True)
+    return (N * s) ** 0.25 * np.exp(1j * rng.uniform(0, 2 * np.pi, shape + (N,)))
+
+
+def _stick_breaking_biases(N, P, sh, s_rows=None):
+    """Output biases near the stick-breaking law of Dirichlet(1/2) (the beta = 0 law), phases near uniform."""
+    from scipy import special
+    k = np.arange(N)
+    b = np.maximum((N - k - 1) / 2, 0.5)
+    b3 = np.zeros((N, 4))
+    b3[:, 0] = special.digamma(0.5) - special.digamma(b)
+    b3[:, 1] = 0.5 * np.log(special.polygamma(1, 0.5) + special.polygamma(1, b))
+    b3[:, 3] = -6.0
+    P[:, sh["ob3"]:sh["ob3"] + 4 * N] = b3.ravel()
+    return P
+
+
+def _randomise_outputs(P, sh, rng, scale=1.0):
+    """Non-trivial output layer so that every term of the density is exercised."""
+    S = P.shape[0]
+    H, Dout = sh["H"], sh["Dout"]
+    P[:, sh["oW3"]:sh["ob3"]] = scale * rng.uniform(-1, 1, (S, Dout * H)) / math.sqrt(H)
+    b3 = np.zeros((S, Dout // 4, 4))
+    b3[..., 0] = rng.normal(-1.0, 0.5, b3.shape[:2])
+    b3[..., 1] = rng.normal(0.0, 0.3, b3.shape[:2])
+    b3[..., 2] = rng.uniform(0, 2 * np.pi, b3.shape[:2])
+    b3[..., 3] = rng.normal(0.0, 1.0, b3.shape[:2])
+    P[:, sh["ob3"]:sh["ob3"] + Dout] = b3.reshape(S, Dout)
+    P[:, sh["oC1"]:sh["oW2"]] = 0.2 * rng.standard_normal((S, sh["oW2"] - sh["oC1"]))
+    return P
+
+
+@pytest.mark.parametrize("N,rows", [(16, 200), (32, 128), (48, 72), (64, 256)])
+def test_learn_eval_matches_oracle(N, rows):
+    """Features, network (tcgen05 GEMMs) and density of the proposal against the FP64 oracle with the
+    BF16 rounding points emulated; gradient of the mean NLL against the oracle's autograd gradient."""
+    S, R, nT, ncold = 2, 8, 4, 3
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    pt = pkg.PT([N] * S, _couplings([N] * S), temps, R, 5, precision="fp32")
+    pt.learn_init(n_cold=ncold, batch=256, data_per_sample=256, seed=9)
+    sh = pt.learn_shape()
+    rng = np.random.default_rng(N + rows)
+    P = _randomise_outputs(pt.learn_params().astype(np.float64), sh, rng).astype(np.float32)
+    pt.set_learn_params(P)
+    assert np.array_equal(pt.learn_params(), P)
+    a = _dirichlet(N, (S, rows), 0.5, rng).astype(np.complex64).astype(np.complex128)
+    cond = rng.integers(0, ncold, (S, rows)).astype(np.int32)
+    lq, ex, g = pt.learn_eval(a, cond, grad=True)
+    M1, M2, M3 = ol.masks(N, sh["H"], 8)
+    for s in range(S):
+        Ps = P[s].astype(np.float64)
+        lq_o, ex_o = ol.logq(Ps, a[s], cond[s], N, sh["H"], ncold, 8, emulate_bf16=True)
+        assert np.abs(ex[s] - ex_o).max() <= 1e-5 * np.abs(ex_o).max() + 1e-4
+        err = np.abs(lq[s] - lq_o)
+        assert err.max() <= 2e-3 + 1e-5 * np.abs(lq_o).max(), (err.max(), np.abs(lq_o).max())
+        go, _ = ol.nll_grad(Ps, a[s], cond[s], N, sh["H"], ncold, 8, emulate_bf16=True)
+        gg = g[s].astype(np.float64)
+        parts = {"W1": (sh["oW1"], sh["ob1"], M1), "b1": (sh["ob1"], sh["oC1"], None), "C1": (sh["oC1"], sh["oW2"], None),
+                 "W2": (sh["oW2"], sh["ob2"], M2), "b2": (sh["ob2"], sh["oW3"], None), "W3": (sh["oW3"], sh["ob3"], M3),
+                 "b3": (sh["ob3"], sh["ob3"] + sh["Dout"], None)}
+        for name, (lo, hi, M) in parts.items():
+            x, y = gg[lo:hi], go[lo:hi]
+            if M is not None:
+                x = x * M.ravel()
+            rel = np.linalg.norm(x - y) / (np.linalg.norm(y) + 1e-30)
+            assert rel < 3e-2, (name, rel)
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_learn_eval_geometric_tails(N):
+    """Configurations whose intensities fall off geometrically (what an untrained proposal draws): the tail
+    sums r_k span many decades, and the density must still follow the FP64 oracle."""
+    S, R, nT, ncold = 1, 4, 2, 1
+    pt = pkg.PT([N] * S, _couplings([N] * S), workload.geometric_ladder(0.5, 1.5, nT), R, 5, precision="fp32")
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=1)
+    sh = pt.learn_shape()
+    rng = np.random.default_rng(N)
+    rows = 64
+    ratio = rng.uniform(0.3, 0.7, rows)
+    s = ratio[:, None] ** np.arange(N)[None, :] * rng.uniform(0.5, 1.5, (rows, N))
+    s /= s.sum(1, keepdims=True)
+    a = ((N * s) ** 0.25 * np.exp(1j * rng.uniform(0, 2 * np.pi, (rows, N))))[None]
+    cond = np.zeros((S, rows), np.int32)
+    P = pt.learn_params().astype(np.float64)
+    lq, ex, _ = pt.learn_eval(a, cond)
+    lq_o, ex_o = ol.logq(P[0], a[0], cond[0], N, sh["H"], ncold, 8, emulate_bf16=True)
+    assert np.allclose(ex[0], ex_o, rtol=1e-5, atol=1e-3), np.abs(ex[0] - ex_o).max()
+    assert np.allclose(lq[0], lq_o, rtol=1e-4, atol=2e-3), np.abs(lq[0] - lq_o).max()
+
+
+def test_learn_eval_rejects_bad_arguments():
+    S, N = 1, 16
+    pt = pkg.PT([N], _couplings([N]), workload.geometric_ladder(0.5, 1.5, 2), 4, 1, precision="fp32")
+    with pytest.raises(pkg.PTError):
+        pt.global_move()  # not initialised
+    with pytest.raises(pkg.PTError):
+        pt.learn_init(n_cold=1, batch=100)  # batch not a multiple of 128
+    pt.learn_init(n_cold=2, batch=128, data_per_sample=128)
+    with pytest.raises(pkg.PTError):
+        pt.learn_init(n_cold=2, batch=128, data_per_sample=128)  # twice
+    a = _dirichlet(N, (S, 8), 0.5, np.random.default_rng(0))
+    with pytest.raises(pkg.PTError):
+        pt.learn_eval(a, np.full((S, 8), 2, np.int32))  # condition out of range
+    with pytest.raises(pkg.PTError):
+        pt.train(4)  # no data collected
+    pt2 = pkg.PT([24], _couplings([24]), workload.geometric_ladder(0.5, 1.5, 2), 4, 1, precision="fp32")
+    with pytest.raises(pkg.PTError):
+        pt2.learn_init(n_cold=1, batch=128)  # N not a multiple of 16
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_global_moves_alone_reach_the_beta0_law(prec):
+    """J = 0 (H = 0 at every temperature): global moves alone, started from Dirichlet(1) intensities, must
+    reach the beta = 0 law of Eq. (8), <Y4> = <sum s_k^2> = 3/(N+2), not Dirichlet(1)'s 2/(N+1)."""
+    N, S, R, nT, ncold = 16, 4, 64, 3, 2
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    import oracle
+    J0 = [np.zeros(len(oracle.enumerate_quads(N)))] * S
+    pt = pkg.PT([N] * S, J0, temps, R, 21, precision=prec)
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
+    sh = pt.learn_shape()
+    P = pt.learn_params().astype(np.float64)
+    P[:, sh["oW3"]:sh["ob3"]] *= 3.0  # keep a configuration-dependent part
+    pt.set_learn_params(_stick_breaking_biases(N, P, sh).astype(np.float32))
+    rng = np.random.default_rng(3)
+    pt.set_state(_dirichlet(N, (S * R * nT,), 1.0, rng).ravel())
+    y4 = []
+    steps = 60
+    for i in range(steps):
+        pt.global_move()
+        if i >= steps // 2:
+            a, E = pt.state()
+            a = a.reshape(S, R, nT, N)[:, :, :ncold]
+            s = np.abs(a) ** 4 / N
+            y4.append((s * s).sum(-1))
+            assert np.all(E == 0)
+    y4 = np.array(y4)  # [step, S, R, ncold]
+    o = pt.observables()
+    acc, att = o["gm_acc"], o["gm_att"]
+    assert np.all(att[:, :ncold] == steps * R) and np.all(att[:, ncold:] == 0)
+    rate = acc[:, :ncold].sum() / att[:, :ncold].sum()
+    assert rate > 0.1, rate
+    m = y4.mean()
+    chain_means = y4.mean(0).ravel()
+    err = 2 * chain_means.std() / math.sqrt(chain_means.size)
+    assert abs(m - 3 / (N + 2)) < 5 * err + 2e-3, (m, 3 / (N + 2), err)
+    assert abs(m - 2 / (N + 1)) > 10 * err
+    # the chains still satisfy the constraint
+    a, _ = pt.state()
+    assert np.allclose((np.abs(a.reshape(-1, N)) ** 4).sum(1), N, rtol=2e-5 if prec == "fp32" else 1e-12)
+
+
+def _block_E(pt, nblocks, sweeps):
+    out = []
+    for _ in range(nblocks):
+        pt.reset_observables()
+        pt.sweep(sweeps)
+        st = pt.observables()["stat"]
+        n = st[..., 0]
+        E = st[..., 1] / n
+        out.append(np.stack([E, st[..., 2] / n - E ** 2, st[..., 4] / n], -1))
+    return np.array(out)
+
+
+def _trained(N, S, R, temps, ncold, seed, steps=4000):
+    pt = pkg.PT([N] * S, _couplings([N] * S), temps, R, seed, precision="fp32", swap_every=8, measure_every=4,
+                resync_every=64)
+    pt.sweep(2048)
+    pt.learn_init(n_cold=ncold, batch=256, data_per_sample=R * ncold * 1024, seed=seed)
+    pt.collect(16, 1024)
+    losses = pt.train(steps, lr=1e-3)
+    return pt, losses
+
+
+def test_training_lowers_the_nll_and_raises_acceptance():
+    N, S, R, nT, ncold = 16, 4, 16, 8, 4
+    temps = workload.geometric_ladder(0.4, 1.6, nT)
+    pt = pkg.PT([N] * S, _couplings([N] * S), temps, R, 11, precision="fp32", swap_every=8)
+    pt.sweep(2048)
+    pt.learn_init(n_cold=ncold, batch=256, data_per_sample=R * ncold * 1024, seed=2)
+    for _ in range(16):
+        pt.global_move()
+    o = pt.observables()
+    before = o["gm_acc"][:, :ncold].sum() / o["gm_att"][:, :ncold].sum()
+    assert pt.learn_shape()["ndata"] == 0
+    pt.collect(16, 1024)
+    assert pt.learn_shape()["ndata"] == 1024 * R * ncold
+    losses = pt.train(4000, lr=1e-3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < losses[:10].mean() - 1.0, (losses[:10].mean(), losses[-50:].mean())
+    pt.reset_observables()
+    for _ in range(16):
+        pt.global_move()
+    o = pt.observables()
+    after = o["gm_acc"][:, :ncold].sum() / o["gm_att"][:, :ncold].sum()
+    print(f"global-move acceptance at the {ncold} coldest T: {before:.4f} untrained -> {after:.4f} trained; "
+          f"NLL {losses[:10].mean():.2f} -> {losses[-50:].mean():.2f}")
+    assert after > before and after > 0.02
+
+
+def test_global_moves_keep_the_thermal_averages():
+    """Finite beta, trained proposal, global moves every 8 sweeps: per (sample, T) thermal averages of E,
+    C_V and Y4 agree with the sweep-only chain (which the FP64 oracle pins) within block errors."""
+    N, S, R, nT, ncold = 16, 4, 16, 8, 4
+    temps = workload.geometric_ladder(0.4, 1.6, nT)
+    pt, _ = _trained(N, S, R, temps, ncold, 13)
+    ref = pkg.PT([N] * S, _couplings([N] * S), temps, R, 14, precision="fp32", swap_every=8, measure_every=4,
+                 resync_every=64)
+    ref.sweep(2048)
+    pt.set_global_every(8)
+    pt.sweep(512)
+    nb, sw = 16, 512
+    g = _block_E(pt, nb, sw)
+    o = _block_E(ref, nb, sw)
+    acc = pt.observables()
+    mg, mo = g.mean(0), o.mean(0)
+    se = np.sqrt(g.var(0, ddof=1) / nb + o.var(0, ddof=1) / nb) + 1e-12
+    z = (mg - mo) / se
+    rate = acc["gm_acc"][:, :ncold].sum() / max(acc["gm_att"][:, :ncold].sum(), 1)
+    print(f"global-move acceptance {rate:.4f}; max |z| {np.abs(z).max():.2f}")
+    assert rate > 0.01
+    assert np.mean(np.abs(z) > 3.0) < 0.05, np.round(z, 2)
+    assert np.abs(z).max() < 5.5, np.round(z, 2)
