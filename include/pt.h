@@ -204,6 +204,13 @@ int pt_global_move(pt_ctx *ctx);
  * resync and before the measurement of the same sweep. */
 int pt_set_global_every(pt_ctx *ctx, int every);
 
+/* Range of the move's first resampled block of modes (8 blocks of N/8 modes): every proposal draws it
+ * uniformly from {lo, ..., hi} (from its own random stream, independently of the state).  Block 0 draws a
+ * whole new configuration under a fresh gauge; block b > 0 keeps modes < b N/8, the gauge and the tail
+ * mass r_{bN/8} of the current configuration and redraws the tail from q's conditionals, with the same
+ * exact acceptance ratio (the kept modes' terms cancel).  Default {0, ..., 7}.  PT_EINVAL outside 0..7. */
+int pt_set_global_blocks(pt_ctx *ctx, int lo, int hi);
+
 /* FP32 master parameters of all samples, [S][psize] (layout from pt_learn_shape): set != 0 uploads them
  * (and refreshes the BF16 copies), set == 0 downloads them. */
 int pt_learn_params(pt_ctx *ctx, float *params, int set);

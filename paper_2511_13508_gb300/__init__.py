@@ -49,7 +49,8 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
            "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
-           "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_gemm_bf16", "pt_energy_fp64_static"]
+           "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_gemm_bf16",
+           "pt_energy_fp64_static"]
 
 _lib = None
 
@@ -88,6 +89,7 @@ def lib() -> ctypes.CDLL:
         L.pt_train.argtypes = [vp, i, d, vp]
         L.pt_global_move.argtypes = [vp]
         L.pt_set_global_every.argtypes = [vp, i]
+        L.pt_set_global_blocks.argtypes = [vp, i, i]
         L.pt_learn_params.argtypes = [vp, vp, i]
         L.pt_learn_shape.argtypes = [vp, vp]
         L.pt_learn_eval.argtypes = [vp, vp, vp, i, vp, vp, vp]
@@ -281,6 +283,15 @@ class PT:
 
     def global_move(self):
         self._c(lib().pt_global_move(self._h))
+
+    def set_global_blocks(self, lo, hi):
+        self._c(lib().pt_set_global_blocks(self._h, int(lo), int(hi)))
+
+    def running_energies(self):
+        """Running FP64 energies of all chains, canonical (s, r, t) order (no recompute)."""
+        E = np.zeros(self.n_chains)
+        self._c(lib().pt_get_state(self._h, None, _p(E)))
+        return E
 
     def set_global_every(self, every):
         self._c(lib().pt_set_global_every(self._h, int(every)))

@@ -138,6 +138,7 @@ struct SegKey {
 struct LearnState {
     ptgb::LearnShape sh{};
     int Mb = 0, ncap = 0, ndata = 0, nprop = 0, rows = 0, global_every = 0, adam_t = 0;
+    int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
     uint64_t seed = 0;
     float *P = nullptr, *Gr = nullptr, *Am = nullptr, *Av = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
@@ -461,19 +462,27 @@ int run_global(pt_ctx *c) {
     ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
     ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
     CK(launch_energy_list(ep, c->S, c->stream));
-    // autoregressive sampling, one pass per block of modes
-    CK(cudaMemsetAsync(L.Xp, 0, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din, c->stream));
-    for (int b = 0; b < ptgb::kLearnBlocks; ++b) {
+    // autoregressive sampling, one pass per block of modes from the first resampled block of each row on;
+    // the blocks below it keep the current configuration's features and variables
+    CK(cudaMemcpyAsync(L.Xp, L.X, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(L.rsamp.u, L.rcur.u, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(L.rsamp.phi, L.rcur.phi, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    for (int b = L.blk_lo; b < ptgb::kLearnBlocks; ++b) {
         if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
         SampleParams sp{};
         sp.O = L.O; sp.rows_per_sample = np; sp.N = sh.N; sp.Dout = sh.Dout; sp.Din = sh.Din; sp.block = b;
+        sp.lo = L.blk_lo; sp.hi = L.blk_hi;
         sp.seed = c->seed; sp.row_id = L.prow; sp.ctl = c->d_ctl; sp.X = L.Xp; sp.u = L.rsamp.u; sp.phi = L.rsamp.phi;
         sp.o_stride = L.rows; sp.x_stride = L.rows;
         CK(launch_sample_block(sp, c->S, c->stream));
     }
     AssembleParams ap{};
     ap.u = L.rsamp.u; ap.phi = L.rsamp.phi; ap.rows_per_sample = np; ap.N = sh.N; ap.seed = c->seed;
+    ap.lo = L.blk_lo; ap.hi = L.blk_hi;
     ap.row_id = L.prow; ap.ctl = c->d_ctl; ap.a = L.a_prop;
+    ap.a_cur = c->d_a; ap.dbl = c->dbl ? 1 : 0; ap.samples = c->d_samples; ap.slot = L.pslot;
     CK(launch_assemble(ap, c->S, c->stream));
     // proposed configurations as stored: features, density, energy
     FeatParams fq = fp;
@@ -1488,6 +1497,18 @@ int pt_set_global_every(pt_ctx *c, int every) {
     if (every < 0) return fail(c, PT_EINVAL, "pt_set_global_every: negative interval");
     if (every > 0 && !c->learn) return fail(c, PT_EINVAL, "pt_set_global_every: call pt_learn_init first");
     if (c->learn) c->learn->global_every = every;
+    return PT_OK;
+}
+
+int pt_set_global_blocks(pt_ctx *c, int lo, int hi) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_set_global_blocks: NULL context");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_set_global_blocks: call pt_learn_init first");
+    if (lo < 0 || hi < lo || hi >= ptgb::kLearnBlocks) return fail(c, PT_EINVAL, "pt_set_global_blocks: need 0 <= lo <= hi <= 7");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    c->learn->blk_lo = lo;
+    c->learn->blk_hi = hi;
+    drop_graphs(c);  // the range is baked into captured segments
     return PT_OK;
 }
 

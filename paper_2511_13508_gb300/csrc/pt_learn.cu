@@ -300,6 +300,7 @@ __global__ void sample_block_kernel(SampleParams p) {
     const int N = p.N, per = N / kLearnBlocks;
     const int64_t grow = (int64_t)s * p.rows_per_sample + row;
     const uint32_t id = p.row_id[grow];
+    if (p.block < first_block(p.seed, id, (uint32_t)p.ctl->global_rounds, N, p.lo, p.hi)) return;
     for (int t = lane; t < per; t += 32) {
         const int k = p.block * per + t;
         const float *o = p.O + ((int64_t)s * p.o_stride + row) * p.Dout + 4 * k;
@@ -329,17 +330,46 @@ cudaError_t launch_sample_block(const SampleParams &p, int S, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// amplitudes: v_k = sigmoid(u_k), s_k = v_k r_k (stick breaking), |a_k| = (N s_k)^(1/4),
-// phi_k = phi~_k + alpha + k theta with a fresh uniform gauge (alpha, theta)
+// amplitudes: v_k = sigmoid(u_k), s_k = v_k r_k (stick breaking), |a_k| = (n s_k)^(1/4),
+// phi_k = phi~_k + alpha + k theta.  With k0 = 8-mode-block start of the first resampled block:
+// k0 = 0: r_0 = 1, n = N, (alpha, theta) fresh and uniform;
+// k0 > 0: modes < k0 copied, r_{k0} = the current tail mass, n = the current sum |a|^4, gauge of the
+// current configuration (alpha = phi_0, theta = phi_1 - phi_0), so the proposal moves only the tail.
 __global__ void assemble_kernel(AssembleParams p) {
     const int s = blockIdx.y, row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= p.rows_per_sample) return;
     const int N = p.N;
     const int64_t grow = (int64_t)s * p.rows_per_sample + row;
-    const u32x4 w = draw(p.seed, p.row_id[grow], (uint32_t)p.ctl->global_rounds, (uint32_t)N, kTagGlobal);
-    const double alpha = kTwoPi * u01(w.x), theta = kTwoPi * u01(w.y);
-    double r = 1.0;
-    for (int k = 0; k < N; ++k) {
+    const uint32_t round = (uint32_t)p.ctl->global_rounds;
+    const int k0 = first_block(p.seed, p.row_id[grow], round, N, p.lo, p.hi) * (N / kLearnBlocks);
+    const SampleDev sd = p.samples[s];
+    const int64_t base = sd.a_off + (int64_t)(p.slot[grow] - sd.chain0) * N;
+    auto cur = [&](int k) {
+        if (p.dbl) return reinterpret_cast<const double2 *>(p.a_cur)[base + k];
+        const float2 v = reinterpret_cast<const float2 *>(p.a_cur)[base + k];
+        return make_double2(v.x, v.y);
+    };
+    double alpha, theta, r = 1.0, n = (double)N;
+    if (k0 == 0) {
+        const u32x4 w = draw(p.seed, p.row_id[grow], round, (uint32_t)N, kTagGlobal);
+        alpha = kTwoPi * u01(w.x);
+        theta = kTwoPi * u01(w.y);
+    } else {
+        const double2 c0 = cur(0), c1 = cur(1);
+        alpha = atan2(c0.y, c0.x);
+        theta = atan2(c1.y, c1.x) - alpha;
+        double tot = 0.0, tail = 0.0;
+        for (int k = N - 1; k >= 0; --k) {
+            const double2 v = cur(k);
+            const double q = v.x * v.x + v.y * v.y;
+            tot += q * q;
+            if (k == k0) tail = tot;
+        }
+        n = tot;
+        r = tail / tot;
+        for (int k = 0; k < k0; ++k) p.a[grow * N + k] = cur(k);
+    }
+    for (int k = k0; k < N; ++k) {
         double sk;
         if (k <= N - 2) {
             const double u = p.u[grow * N + k];
@@ -348,7 +378,7 @@ __global__ void assemble_kernel(AssembleParams p) {
         } else {
             sk = r;
         }
-        const double A = sqrt(sqrt((double)N * fmax(sk, 0.0)));
+        const double A = sqrt(sqrt(n * fmax(sk, 0.0)));
         const double ph = (double)p.phi[grow * N + k] + alpha + (double)k * theta;
         double sn, cs;
         sincos(ph, &sn, &cs);

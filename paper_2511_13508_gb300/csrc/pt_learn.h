@@ -100,10 +100,19 @@ struct GatherParams {
 };
 cudaError_t launch_gather(const GatherParams &p, int S, cudaStream_t s);
 
-// One sampling pass: fill the variables of mode block b from the network outputs (rows = proposals).
+// First resampled block of a proposal row: uniform on [lo, hi], drawn from the row's stream.  Blocks below
+// it keep the current configuration (and its gauge); block 0 resamples everything under a fresh gauge.
+__device__ __forceinline__ int first_block(uint64_t seed, uint32_t id, uint32_t round, int N, int lo, int hi) {
+    const u32x4 w = draw(seed, id, round, (uint32_t)(N + 2), kTagGlobal);
+    return lo + (int)(((uint64_t)w.x * (uint64_t)(hi - lo + 1)) >> 32);
+}
+
+// One sampling pass: fill the variables of mode block b from the network outputs (rows = proposals);
+// rows whose first resampled block is above b keep the current values already in X, u, phi.
 struct SampleParams {
     const float *O;
     int rows_per_sample, N, Dout, Din, block;
+    int lo, hi;              // range of the first resampled block
     uint64_t seed;
     const uint32_t *row_id;  // [S][rows] chain ids (stream of the draws)
     const Control *ctl;      // global_rounds = round of the draws
@@ -113,13 +122,20 @@ struct SampleParams {
 };
 cudaError_t launch_sample_block(const SampleParams &p, int S, cudaStream_t s);
 
-// Amplitudes of the proposals from (u, phi~) and a fresh uniform gauge.
+// Amplitudes of the proposals from (u, phi~): modes below the first resampled block k0 are copied from the
+// current configuration, the tail mass r_{k0} is the current one, and the gauge is the current one
+// (fresh and uniform when k0 = 0).
 struct AssembleParams {
     const float *u, *phi;
     int rows_per_sample, N;
+    int lo, hi;
     uint64_t seed;
     const uint32_t *row_id;
     const Control *ctl;
+    const void *a_cur;       // chain states (float2 or double2)
+    int dbl;
+    const SampleDev *samples;
+    const int *slot;         // [S][rows] chain slots
     double2 *a;              // [S][rows][N]
 };
 cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s);

@@ -155,9 +155,24 @@ def test_learn_eval_rejects_bad_arguments():
         pt.learn_eval(a, np.full((S, 8), 2, np.int32))  # condition out of range
     with pytest.raises(pkg.PTError):
         pt.train(4)  # no data collected
+    for lo, hi in ((3, 2), (0, 8), (-1, 3)):
+        with pytest.raises(pkg.PTError):
+            pt.set_global_blocks(lo, hi)
     pt2 = pkg.PT([24], _couplings([24]), workload.geometric_ladder(0.5, 1.5, 2), 4, 1, precision="fp32")
     with pytest.raises(pkg.PTError):
         pt2.learn_init(n_cold=1, batch=128)  # N not a multiple of 16
+
+
+def _j0_learner(N, S, R, nT, ncold, prec, seed):
+    import oracle
+    J0 = [np.zeros(len(oracle.enumerate_quads(N)))] * S
+    pt = pkg.PT([N] * S, J0, workload.geometric_ladder(0.5, 1.5, nT), R, seed, precision=prec)
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
+    sh = pt.learn_shape()
+    P = pt.learn_params().astype(np.float64)
+    P[:, sh["oW3"]:sh["ob3"]] *= 3.0  # keep a configuration-dependent part
+    pt.set_learn_params(_stick_breaking_biases(N, P, sh).astype(np.float32))
+    return pt
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -165,15 +180,8 @@ def test_global_moves_alone_reach_the_beta0_law(prec):
     """J = 0 (H = 0 at every temperature): global moves alone, started from Dirichlet(1) intensities, must
     reach the beta = 0 law of Eq. (8), <Y4> = <sum s_k^2> = 3/(N+2), not Dirichlet(1)'s 2/(N+1)."""
     N, S, R, nT, ncold = 16, 4, 64, 3, 2
-    temps = workload.geometric_ladder(0.5, 1.5, nT)
-    import oracle
-    J0 = [np.zeros(len(oracle.enumerate_quads(N)))] * S
-    pt = pkg.PT([N] * S, J0, temps, R, 21, precision=prec)
-    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
-    sh = pt.learn_shape()
-    P = pt.learn_params().astype(np.float64)
-    P[:, sh["oW3"]:sh["ob3"]] *= 3.0  # keep a configuration-dependent part
-    pt.set_learn_params(_stick_breaking_biases(N, P, sh).astype(np.float32))
+    pt = _j0_learner(N, S, R, nT, ncold, prec, 21)
+    pt.set_global_blocks(0, 0)
     rng = np.random.default_rng(3)
     pt.set_state(_dirichlet(N, (S * R * nT,), 1.0, rng).ravel())
     y4 = []
@@ -200,6 +208,53 @@ def test_global_moves_alone_reach_the_beta0_law(prec):
     # the chains still satisfy the constraint
     a, _ = pt.state()
     assert np.allclose((np.abs(a.reshape(-1, N)) ** 4).sum(1), N, rtol=2e-5 if prec == "fp32" else 1e-12)
+
+
+@pytest.mark.parametrize("prec,lo,hi", [("fp32", 7, 7), ("fp64", 2, 5), ("fp32", 1, 7)])
+def test_tail_moves_reach_the_conditional_beta0_law(prec, lo, hi):
+    """Tail moves keep the modes below the first resampled block.  Under the beta = 0 law the fractions
+    s_k / r_m of the modes k >= m = hi N/8 (always resampled) are Dirichlet(1/2) over those N - m modes
+    whatever the head, so <sum (s_k / r_m)^2> = 3/(n+2), n = N - m.  The chains start with these fractions
+    drawn from Dirichlet(1) (2/(n+1)) and the head and tail mass from the beta = 0 law; the head must not move."""
+    N, S, R, nT, ncold = 32, 4, 64, 3, 2
+    pt = _j0_learner(N, S, R, nT, ncold, prec, 22)
+    pt.set_global_blocks(lo, hi)
+    m = hi * N // 8
+    n = N - m
+    rng = np.random.default_rng(5)
+    C = S * R * nT
+    s = _dirichlet(N, (C,), 0.5, rng)
+    s = np.abs(s) ** 4 / N
+    g = rng.exponential(size=(C, n))
+    s[:, m:] = s[:, m:].sum(1, keepdims=True) * g / g.sum(1, keepdims=True)
+    a0 = (N * s) ** 0.25 * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    pt.set_state(a0.ravel())
+    a_start = pt.state()[0].reshape(S, R, nT, N)
+    stat = []
+    steps = 60
+    for i in range(steps):
+        pt.global_move()
+        if i >= steps // 2:
+            a = pt.state()[0].reshape(S, R, nT, N)[:, :, :ncold]
+            f = np.abs(a[..., m:]) ** 4
+            f = f / f.sum(-1, keepdims=True)
+            stat.append((f * f).sum(-1))
+    a_end = pt.state()[0].reshape(S, R, nT, N)
+    lo_k = lo * N // 8
+    # modes below the lowest first block never move; the warmer chains do not move at all
+    assert np.array_equal(a_end[:, :, :, :lo_k], a_start[:, :, :, :lo_k])
+    assert np.array_equal(a_end[:, :, ncold:], a_start[:, :, ncold:])
+    o = pt.observables()
+    rate = o["gm_acc"][:, :ncold].sum() / o["gm_att"][:, :ncold].sum()
+    assert rate > 0.1, rate
+    stat = np.array(stat)
+    mean = stat.mean()
+    cm = stat.mean(0).ravel()
+    err = 2 * cm.std() / math.sqrt(cm.size)
+    assert abs(mean - 3 / (n + 2)) < 5 * err + 2e-3, (mean, 3 / (n + 2), err)
+    assert abs(mean - 2 / (n + 1)) > 10 * err
+    tot = (np.abs(a_end.reshape(-1, N)) ** 4).sum(1)
+    assert np.allclose(tot, N, rtol=2e-5 if prec == "fp32" else 1e-12)
 
 
 def _block_E(pt, nblocks, sweeps):
