@@ -34,6 +34,9 @@ CPU_SAMPLE_SECONDS = 15.0
 
 
 # ------------------------------------------------------------------------------------------- accounting
+METRIC = "chain-sweeps/s at N=256 vs plain FP64; eff. samples/s learned vs plain PT"
+
+
 def flops_per_chain_sweep(N: int) -> float:
     """Algorithmic FP32 flops of one sweep (N/2 pair updates) of the pair-factored field evaluation,
     averaged exactly over the pair distribution (j uniform, k uniform among the other modes):
@@ -248,6 +251,26 @@ def run_gpu(args, rank, world, dist):
                 e2e=e2e, fl=fl)
 
 
+def learned_leg():
+    """Effective samples/s at the coldest temperature, learned global move vs plain PT, on the learned-proposal
+    workload (N=64, 16 samples x 32 T [0.3,1.6] x 2 replicas; 2^14 training configurations per sample from
+    the 8 coldest temperatures; a global move every 8 sweeps)."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import gain, workload
+    W = workload.workloads()["n64_learned"]
+    nq = len(pkg.enumerate_quads(W.Ns[0]))
+    Js = [workload.couplings(W.Ns[0], nq, s) for s in W.seeds]
+    pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 4401, precision="fp32", stream=torch.cuda.Stream(),
+                swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
+    r = gain.measure(pt, n_cold=W.extra["n_cold"], global_every=W.extra["global_every"],
+                     train_configs=W.extra["train_configs"], train_steps=6000)
+    pt.close()
+    r["workload"] = "n64_learned: N=64, 16 samples x 32 T [0.3,1.6] x 2 replicas, FP32"
+    r["unit"] = "effective samples/s of E at the coldest T"
+    return r
+
+
 def profile_case():
     """Three launches of the sweep kernel (one sweep each) on half the bench workload: 8 samples
     (176 MB of couplings, larger than L2), 768 chains; no measurement, resync or swap."""
@@ -274,6 +297,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal ESS comparison")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     args = ap.parse_args()
@@ -294,7 +318,7 @@ def main():
             cpu_oracle_rate(target_seconds=per / 4)
         vals = [cpu_oracle_rate(target_seconds=per) for _ in range(args.steps)]
         v = statistics.mean(x["value"] for x in vals)
-        line = {"metric": "chain-sweeps/s at N=256", "value": v, "unit": "chain-sweeps/s", "n_gpus": 0,
+        line = {"metric": METRIC, "value": v, "unit": "chain-sweeps/s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
                 "impl": "reference",
@@ -315,8 +339,11 @@ def main():
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     r = run_gpu(args, rank, world, dist)
+    learned = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        learned = learned_leg()
     if rank == 0:
-        line = {"metric": "chain-sweeps/s at N=256", "value": r["value"], "unit": "chain-sweeps/s",
+        line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
@@ -330,7 +357,8 @@ def main():
                 "clocks": r["clocks"],
                 "gpu_launches": 5 * args.steps,
                 "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
-                                   "speedup_fp32": r["value"] / world / r["plain_rate"]}}
+                                   "speedup_fp32": r["value"] / world / r["plain_rate"]},
+                "learned_vs_plain": learned}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -4,11 +4,13 @@
 //
 //   D[b] (M x N, FP32) = A[b] (M x K, BF16, row-major = K-major) * B[b]^T (B: N x K, BF16, K-major)
 //
-// One thread block computes a 128 x N tile (N <= 256) with the accumulator in tensor memory: the
-// operands are staged in shared memory in the canonical K-major no-swizzle layout (8 x 16-byte core
-// matrices), one elected thread issues tcgen05.mma (M = 128, N, K = 16 per instruction) and commits to
-// an mbarrier, and four warps read the accumulator back with tcgen05.ld (warp w owns lanes 32w..32w+31)
-// for the epilogue.
+// One thread block computes a 128 x 64 tile with the accumulator in tensor memory: the
+// operands are staged by asynchronous copies (cp.async, zero-filled outside the matrix) in shared memory
+// in the canonical K-major no-swizzle layout (8 x 16-byte core matrices), two stages of K = 128 so that the
+// copies of the next chunk overlap the MMAs of this one; one elected thread issues tcgen05.mma (M = 128,
+// N = 64, K = 16 per instruction) and commits to the stage's mbarrier; four warps read the accumulator back
+// with tcgen05.ld (warp w owns lanes 32w..32w+31) and transpose it through shared memory so that every
+// global store of the epilogue is coalesced.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include "pt_common.cuh"
@@ -19,7 +21,8 @@ namespace ptgb {
 namespace {
 
 constexpr int kGemmM = 128;   // rows per thread block (= TMEM lanes)
-constexpr int kGemmKC = 64;   // K per shared-memory chunk (4 MMAs of K = 16)
+constexpr int kGemmKC = 128;  // K per pipeline stage (8 MMAs of K = 16)
+constexpr int kGemmNT = 64;   // output columns per thread block (the MMA's N); two stages of 48 KB
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,63 +61,98 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Copies rows [r0, r0+rows) x K-chunk [k0, k0+KC) of a row-major BF16 matrix (leading dimension ld,
-// valid rows < nrows, valid columns < K) into the canonical layout: element (r, k) at
-// (k / 8) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes.  Out-of-range parts are zero.
-__device__ __forceinline__ void stage_tile(unsigned char *dst, const __nv_bfloat16 *src, int ld, int r0, int rows,
-                                          int nrows, int k0, int K, uint32_t lbo) {
-    const int pieces = rows * (kGemmKC / 8);
+// Issues the asynchronous copies of rows [r0, r0+rows) x K-chunk [k0, k0+KC) of a row-major BF16 matrix
+// (leading dimension ld, valid rows < nrows, valid columns < K) into the canonical layout: element (r, k)
+// at (k / 8) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes.  Out-of-range parts are zero-filled.
+// Lane l of a warp takes K-group (l & 1) of row (l >> 1): 32 contiguous bytes of one row per lane pair.
+__device__ __forceinline__ void stage_async(uint32_t dst, const __nv_bfloat16 *src, int ld, int r0, int rows,
+                                           int nrows, int k0, int K, uint32_t lbo) {
+    constexpr int kGroups = kGemmKC / 8;
+    const int pieces = rows * kGroups;
     for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
-        const int r = p / (kGemmKC / 8), kg = p % (kGemmKC / 8);
+        // p -> (row, K-group): bit 0 = low bit of the group, bits 1..4 = row within 16, then the rest
+        const int kg = ((p >> 5) % (kGroups / 2)) * 2 + (p & 1);
+        const int r = (p >> 5) / (kGroups / 2) * 16 + ((p >> 1) & 15);
         const int gr = r0 + r, gk = k0 + kg * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < nrows && gk < K) v = *reinterpret_cast<const uint4 *>(src + (int64_t)gr * ld + gk);
-        *reinterpret_cast<uint4 *>(dst + kg * lbo + (r / 8) * 128 + (r % 8) * 16) = v;
+        const bool ok = gr < nrows && gk < K;
+        const __nv_bfloat16 *g = ok ? src + (int64_t)gr * ld + gk : src;
+        const uint32_t d = dst + kg * lbo + (r / 8) * 128 + (r % 8) * 16;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(ok ? 16 : 0) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Bounded wait on an mbarrier phase; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(GemmParams p) {
+// Two-stage pipeline: the copies of chunk c+1 are in flight while the tensor cores work on chunk c.
+__global__ void __launch_bounds__(128, 2) gemm_bf16_tc_kernel(GemmParams p) {
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_base_slot;
-    const int b = blockIdx.z, m0 = blockIdx.x * kGemmM;
-    const int N = p.N, K = p.K;
+    const int b = blockIdx.z, m0 = blockIdx.x * kGemmM, n0 = blockIdx.y * kGemmNT;
+    const int N = p.N, K = p.K, NT = min(kGemmNT, N - n0);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    unsigned char *sA = gsm;                                   // 128 x 64 BF16 = 16 KB
-    unsigned char *sB = gsm + kGemmM * kGemmKC * 2;            // N x 64 BF16 <= 32 KB
-    const uint32_t lboA = (kGemmM / 8) * 128, lboB = (uint32_t)((N + 7) / 8) * 128;
+    constexpr uint32_t kStageA = kGemmM * kGemmKC * 2, kStage = kStageA + kGemmNT * kGemmKC * 2;
+    const uint32_t s0 = smem_addr(gsm);
+    const uint32_t lboA = (kGemmM / 8) * 128, lboB = (uint32_t)(NT / 8) * 128;
     const __nv_bfloat16 *A = p.A + (int64_t)b * p.strideA;
-    const __nv_bfloat16 *Bm = p.B + (int64_t)b * p.strideB;
+    const __nv_bfloat16 *Bm = p.B + (int64_t)b * p.strideB + (int64_t)n0 * p.ldb;  // rows n0 .. n0+NT of B
 
-    // tensor-memory accumulator: 256 columns x 128 lanes of FP32
+    // tensor-memory accumulator: 64 columns x 128 lanes of FP32
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_base_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&tmem_base_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 0) mbar_init1(&mbar);
+    if (threadIdx.x == 0) { mbar_init1(&mbar[0]); mbar_init1(&mbar[1]); }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_slot;
-    const uint32_t idesc = make_idesc(N);
-    uint32_t phase = 0;
-    bool timed_out = false;
+    const uint32_t idesc = make_idesc(NT);
+    uint32_t phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};  // a commit on the stage's barrier not yet waited for
+    bool ok = true;
+    const int nchunks = (K + kGemmKC - 1) / kGemmKC;
 
-    for (int k0 = 0; k0 < K; k0 += kGemmKC) {
-        stage_tile(sA, A, p.lda, m0, kGemmM, p.M, k0, K, lboA);
-        stage_tile(sB, Bm, p.ldb, 0, N, N, k0, K, lboB);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+    stage_async(s0, A, p.lda, m0, kGemmM, p.M, 0, K, lboA);
+    stage_async(s0 + kStageA, Bm, p.ldb, 0, NT, NT, 0, K, lboB);
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int st = c & 1;
+        if (c + 1 < nchunks) {
+            const int nx = (c + 1) & 1;
+            if (c >= 1) {  // the other stage was read by chunk c-1's MMAs
+                ok = mbar_wait(&mbar[nx], phase[nx]);
+                phase[nx] ^= 1u;
+                pend[nx] = false;
+                if (!ok) break;
+            }
+            const uint32_t base = s0 + nx * kStage;
+            stage_async(base, A, p.lda, m0, kGemmM, p.M, (c + 1) * kGemmKC, K, lboA);
+            stage_async(base + kStageA, Bm, p.ldb, 0, NT, NT, (c + 1) * kGemmKC, K, lboB);
+            asm volatile("cp.async.wait_group 2;" ::: "memory");  // chunk c's two groups have landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core reads
         __syncthreads();
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int ksteps = min(kGemmKC, K - k0 + 15) / 16;
-            for (int t = 0; t < ksteps && t < kGemmKC / 16; ++t) {
-                const uint64_t da = make_sdesc(smem_addr(sA) + t * 2 * lboA, lboA, 128);
-                const uint64_t db = make_sdesc(smem_addr(sB) + t * 2 * lboB, lboB, 128);
-                const uint32_t acc = (k0 > 0 || t > 0) ? 1u : 0u;
+            const uint32_t sa = s0 + st * kStage, sb = sa + kStageA;
+            const int k0 = c * kGemmKC;
+            const int ksteps = (min(kGemmKC, K - k0) + 15) / 16;
+            for (int t = 0; t < ksteps; ++t) {
+                const uint64_t da = make_sdesc(sa + t * 2 * lboA, lboA, 128);
+                const uint64_t db = make_sdesc(sb + t * 2 * lboB, lboB, 128);
+                const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred pacc;\n\tsetp.ne.b32 pacc, %4, 0;\n\t"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pacc;\n\t}" ::"r"(tmem),
@@ -122,55 +160,87 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(GemmParams p) {
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&mbar))
+                             smem_addr(&mbar[st]))
                          : "memory");
         }
-        // wait for the MMAs (bounded); every thread polls so the shared tiles may be overwritten after
-        const unsigned long long t0 = global_ns();
-        while (!mbar_test(&mbar, phase)) {
-            if (global_ns() - t0 > kWaitNs) { timed_out = true; break; }
-        }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
+        pend[st] = true;
     }
-    if (timed_out && threadIdx.x == 0 && p.err) atomicCAS(p.err, 0, kErrTimeout);
-
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane, 32 columns at a time
-    const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 32) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < p.M) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // drain every outstanding commit (bounded), so no MMA or barrier arrival outlives the block
+    for (int st = 0; st < 2; ++st)
+        if (pend[st] && !mbar_wait(&mbar[st], phase[st])) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0 && p.err) atomicCAS(p.err, 0, kErrTimeout);
+    } else {
+        // epilogue.  Phase 1 (lane = row): warp w reads TMEM lanes 32w..32w+31, 32 columns at a time, applies
+        // bias / conditional bias / gate, writes the transposed BF16 copy (coalesced along rows) and parks the
+        // values in a 32 x 33 shared tile.  Phase 2 (lane = column): row-major FP32 and BF16 stores, coalesced.
+        float *tile = reinterpret_cast<float *>(gsm) + warp * (32 * 33);
+        const int row = m0 + warp * 32 + lane;
+        const bool relu = p.mode == kEpiRelu;
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const bool live = row < p.M;
+            const float *cb = (p.cbias && live)
+                                  ? p.cbias + (int64_t)b * p.strideCbias + (int64_t)p.cond[(int64_t)b * p.strideCond + row] * N
+                                  : nullptr;
+            const float *gt = (p.mode == kEpiGate && live)
+                                  ? p.gate + (int64_t)b * p.strideGate + (int64_t)row * p.ldgate : nullptr;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const int col = c0 + q;
-                if (col < N) gemm_epilogue(p, b, row, col, __uint_as_float(r[q]));
+                const int col = n0 + c0 + q;
+                float v = __uint_as_float(r[q]);
+                if (p.mode == kEpiGate) {
+                    v = (gt && col < N && gt[col] > 0.f) ? v : 0.f;
+                } else {
+                    if (p.bias && col < N) v += p.bias[(int64_t)b * p.strideBias + col];
+                    if (cb && col < N) v += cb[col];
+                }
+                tile[lane * 33 + q] = v;
+                if (p.HT && live && col < N)
+                    p.HT[(int64_t)b * p.strideHT + (int64_t)col * p.ldht + row] = __float2bfloat16_rn(relu ? fmaxf(v, 0.f) : v);
             }
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row2 = m0 + warp * 32 + rr;
+                if (row2 >= p.M || col >= N) continue;
+                const float v = tile[rr * 33 + lane];
+                if (p.D) p.D[(int64_t)b * p.strideD + (int64_t)row2 * p.ldd + col] = v;
+                if (p.H) p.H[(int64_t)b * p.strideH + (int64_t)row2 * p.ldh + col] = __float2bfloat16_rn(relu ? fmaxf(v, 0.f) : v);
+            }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s) {
     if (p.N < 16 || p.N > 256 || (p.N % 16) || p.K < 16 || (p.K % 8) || p.M < 1 || batch < 1)
         return cudaErrorInvalidValue;
-    const size_t sm = (size_t)kGemmM * kGemmKC * 2 + (size_t)256 * kGemmKC * 2;
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((p.M + kGemmM - 1) / kGemmM, 1, batch);
+    constexpr size_t sm = 2 * ((size_t)kGemmM * kGemmKC * 2 + (size_t)kGemmNT * kGemmKC * 2);
+    static bool attr_set = false;  // per process; the attribute is a property of the function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((p.M + kGemmM - 1) / kGemmM, (p.N + kGemmNT - 1) / kGemmNT, batch);
     gemm_bf16_tc_kernel<<<grid, 128, sm, s>>>(p);
     return cudaGetLastError();
 }

@@ -37,20 +37,6 @@ struct GemmParams {
     int *err;
 };
 
-__device__ __forceinline__ void gemm_epilogue(const GemmParams &p, int b, int row, int col, float v) {
-    if (p.mode == kEpiGate) {
-        const float g = p.gate[(int64_t)b * p.strideGate + (int64_t)row * p.ldgate + col];
-        v = g > 0.f ? v : 0.f;
-    } else {
-        if (p.bias) v += p.bias[(int64_t)b * p.strideBias + col];
-        if (p.cbias) v += p.cbias[(int64_t)b * p.strideCbias + (int64_t)p.cond[(int64_t)b * p.strideCond + row] * p.N + col];
-    }
-    if (p.D) p.D[(int64_t)b * p.strideD + (int64_t)row * p.ldd + col] = v;
-    if (p.mode == kEpiRelu) v = fmaxf(v, 0.f);
-    if (p.H) p.H[(int64_t)b * p.strideH + (int64_t)row * p.ldh + col] = __float2bfloat16_rn(v);
-    if (p.HT) p.HT[(int64_t)b * p.strideHT + (int64_t)col * p.ldht + row] = __float2bfloat16_rn(v);
-}
-
 cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s);
 
 }  // namespace ptgb

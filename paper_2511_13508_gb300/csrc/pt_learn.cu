@@ -16,6 +16,8 @@ constexpr float kLog2PiHalf = 0.91893853320467274178f;  // log(2 pi) / 2
 constexpr float kRhoMax = 0.98f;
 constexpr float kUScale = 0.25f;                          // input scale of logit(v)
 
+// uniform in (0, 1) from the top 24 bits of a Philox word (FP32 draws)
+__device__ __forceinline__ float u01f(uint32_t w) { return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f); }
 __device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 __device__ __forceinline__ float wrap2pi(float x) { return x - kTwoPiF * floorf(x / kTwoPiF); }
 
@@ -308,12 +310,12 @@ __global__ void sample_block_kernel(SampleParams p) {
         float u = 0.f, ph = 0.f;
         if (k <= N - 2) {
             const float ls = fminf(fmaxf(o[1], -7.f), 3.f);
-            const float eps = (float)(sqrt(-2.0 * log(u01(w.x))) * cos(kTwoPi * u01(w.y)));
+            const float eps = sqrtf(-2.f * logf(u01f(w.x))) * cosf(kTwoPiF * u01f(w.y));  // Box-Muller
             u = o[0] + expf(ls) * eps;
         }
         if (k >= 2) {
             const float rho = kRhoMax / (1.f + expf(-o[3]));
-            const float t1 = tanf(3.14159265358979323846f * ((float)u01(w.z) - 0.5f));
+            const float t1 = tanf(3.14159265358979323846f * (u01f(w.z) - 0.5f));
             ph = wrap2pi(o[2] + 2.f * atanf((1.f - rho) / (1.f + rho) * t1));
         }
         p.u[grow * N + k] = u;
@@ -335,8 +337,9 @@ cudaError_t launch_sample_block(const SampleParams &p, int S, cudaStream_t s) {
 // k0 = 0: r_0 = 1, n = N, (alpha, theta) fresh and uniform;
 // k0 > 0: modes < k0 copied, r_{k0} = the current tail mass, n = the current sum |a|^4, gauge of the
 // current configuration (alpha = phi_0, theta = phi_1 - phi_0), so the proposal moves only the tail.
+// One warp per row, two modes per lane; r_k is an exclusive product scan over the lanes.
 __global__ void assemble_kernel(AssembleParams p) {
-    const int s = blockIdx.y, row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y, row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (row >= p.rows_per_sample) return;
     const int N = p.N;
     const int64_t grow = (int64_t)s * p.rows_per_sample + row;
@@ -344,51 +347,94 @@ __global__ void assemble_kernel(AssembleParams p) {
     const int k0 = first_block(p.seed, p.row_id[grow], round, N, p.lo, p.hi) * (N / kLearnBlocks);
     const SampleDev sd = p.samples[s];
     const int64_t base = sd.a_off + (int64_t)(p.slot[grow] - sd.chain0) * N;
-    auto cur = [&](int k) {
-        if (p.dbl) return reinterpret_cast<const double2 *>(p.a_cur)[base + k];
-        const float2 v = reinterpret_cast<const float2 *>(p.a_cur)[base + k];
-        return make_double2(v.x, v.y);
-    };
-    double alpha, theta, r = 1.0, n = (double)N;
+    double2 cur[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    if (k0 > 0)
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            if (k < N) {
+                if (p.dbl) cur[q] = reinterpret_cast<const double2 *>(p.a_cur)[base + k];
+                else { const float2 v = reinterpret_cast<const float2 *>(p.a_cur)[base + k]; cur[q] = make_double2(v.x, v.y); }
+            }
+        }
+    double alpha, theta, r0 = 1.0, n = (double)N;
     if (k0 == 0) {
         const u32x4 w = draw(p.seed, p.row_id[grow], round, (uint32_t)N, kTagGlobal);
         alpha = kTwoPi * u01(w.x);
         theta = kTwoPi * u01(w.y);
     } else {
-        const double2 c0 = cur(0), c1 = cur(1);
-        alpha = atan2(c0.y, c0.x);
-        theta = atan2(c1.y, c1.x) - alpha;
         double tot = 0.0, tail = 0.0;
-        for (int k = N - 1; k >= 0; --k) {
-            const double2 v = cur(k);
-            const double q = v.x * v.x + v.y * v.y;
-            tot += q * q;
-            if (k == k0) tail = tot;
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            const double u = cur[q].x * cur[q].x + cur[q].y * cur[q].y;
+            tot += u * u;
+            if (k >= k0) tail += u * u;
         }
+        tot = warp_sumd(tot);
+        tail = warp_sumd(tail);
         n = tot;
-        r = tail / tot;
-        for (int k = 0; k < k0; ++k) p.a[grow * N + k] = cur(k);
+        r0 = tail / tot;
+        const double a0 = __shfl_sync(0xffffffffu, atan2(cur[0].y, cur[0].x), 0);
+        const double a1 = __shfl_sync(0xffffffffu, atan2(cur[0].y, cur[0].x), 1);
+        alpha = a0;
+        theta = a1 - a0;
     }
-    for (int k = k0; k < N; ++k) {
-        double sk;
-        if (k <= N - 2) {
-            const double u = p.u[grow * N + k];
-            sk = r / (1.0 + exp(-u));  // v_k r_k
-            r = r / (1.0 + exp(u));    // r_{k+1} = r_k (1 - v_k), without cancellation
-        } else {
-            sk = r;
+    // per mode k >= k0: v_k and 1 - v_k from one exponential in (0, 1] (v + (1-v) = 1 to FP64 rounding):
+    // v = 1/(1+t), 1-v = t/(1+t) with t = e^{-u} (u >= 0); v = w/(1+w), 1-v = 1/(1+w) with w = e^{u} (u < 0)
+    double v[2], f[2];
+    for (int q = 0; q < 2; ++q) {
+        const int k = lane + 32 * q;
+        v[q] = 0.0;
+        f[q] = 1.0;
+        if (k >= k0 && k <= N - 2) {
+            const float u = p.u[grow * N + k];
+            const double e = (double)expf(-fabsf(u)), d = 1.0 / (1.0 + e);
+            v[q] = u >= 0.f ? d : e * d;
+            f[q] = u >= 0.f ? e * d : d;
+        } else if (k == N - 1) {
+            v[q] = 1.0;  // the last mode takes the remaining mass
         }
+    }
+    // exclusive product scan of f over modes 0..63 (f = 1 below k0): r_k = r_{k0} prod_{k0 <= i < k} f_i
+    double x0 = f[0], x1 = f[1];
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= o) { x0 *= y0; x1 *= y1; }
+    }
+    const double low_total = __shfl_sync(0xffffffffu, x0, 31);  // product over modes 0..31
+    const double e0 = __shfl_up_sync(0xffffffffu, x0, 1), e1 = __shfl_up_sync(0xffffffffu, x1, 1);
+    const double P[2] = {lane ? e0 : 1.0, (lane ? e1 : 1.0) * low_total};
+    for (int q = 0; q < 2; ++q) {
+        const int k = lane + 32 * q;
+        if (k >= N) continue;
+        if (k < k0) {
+            p.a[grow * N + k] = cur[q];
+            continue;
+        }
+        const double sk = r0 * P[q] * v[q];
         const double A = sqrt(sqrt(n * fmax(sk, 0.0)));
-        const double ph = (double)p.phi[grow * N + k] + alpha + (double)k * theta;
+        // phi~_k = phi_k - phi_0 - k (phi_1 - phi_0): errors in the phases of modes 0 and 1 come back k-fold
+        // when the density is evaluated on the stored configuration, so those two are formed in FP64; the
+        // others carry an FP32 rounding of the draw (as the stored draw itself does).  The unit vector is
+        // renormalised in FP64 so that |a_k|^4 = n s_k holds to FP64 rounding.
+        double ph = (double)p.phi[grow * N + k] + alpha + (double)k * theta;
         double sn, cs;
-        sincos(ph, &sn, &cs);
+        if (k < 2) {
+            sincos(ph, &sn, &cs);
+        } else {
+            ph -= kTwoPi * floor(ph / kTwoPi);
+            float sf, cf;
+            sincosf((float)ph, &sf, &cf);
+            const double inv = 1.0 / sqrt((double)cf * cf + (double)sf * sf);
+            sn = sf * inv;
+            cs = cf * inv;
+        }
         p.a[grow * N + k] = make_double2(A * cs, A * sn);
     }
 }
 
 cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
-    dim3 grid((p.rows_per_sample + 63) / 64, S);
-    assemble_kernel<<<grid, 64, 0, s>>>(p);
+    dim3 grid((p.rows_per_sample + 3) / 4, S);
+    assemble_kernel<<<grid, 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 

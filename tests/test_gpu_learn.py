@@ -328,3 +328,19 @@ def test_global_moves_keep_the_thermal_averages():
     assert rate > 0.01
     assert np.mean(np.abs(z) > 3.0) < 0.05, np.round(z, 2)
     assert np.abs(z).max() < 5.5, np.round(z, 2)
+
+
+def test_gain_measurement_reports_ess_of_both_methods():
+    """What the trained network gains over plain PT: effective samples/s of E at the coldest T (Sokal
+    tau_int), both methods on the same ensemble; the averages must agree, the gain is reported as measured."""
+    from paper_2511_13508_gb300 import gain
+    N, S, R, nT = 16, 4, 8, 8
+    temps = workload.geometric_ladder(0.4, 1.6, nT)
+    pt = pkg.PT([N] * S, _couplings([N] * S), temps, R, 31, precision="fp32", swap_every=16)
+    r = gain.measure(pt, n_cold=4, global_every=8, train_configs=R * 4 * 512, train_steps=3000, batch=256,
+                     burn_in=2048, series=2048, rate_sweeps=2048)
+    print({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()})
+    assert r["ess_per_s_plain"] > 0 and r["ess_per_s_learned"] > 0
+    assert r["nll_last"] < r["nll_first"]
+    assert max(r["acceptance_coldest"]) > 0.01
+    assert abs(r["mean_E_coldest_plain"] - r["mean_E_coldest_learned"]) < 0.05 * abs(r["mean_E_coldest_plain"])
