@@ -138,7 +138,7 @@ template <typename V> __device__ __forceinline__ void cfma_conj(V &h, V m, V acc
 // (MODE & 2), and the j-k cross terms (with the j field).  as = shared amplitude table; Jj, Jk =
 // column-major blocks.  The x offset i runs outside, the row r inside, so the 2*TS row accumulators
 // are independent chains of fused multiply-adds.
-template <typename real, int RS, int MODE>
+template <typename real, int RS, int MODE, bool WB>
 __device__ __forceinline__ void process_block(const typename vec2<real>::type *__restrict__ as, int c, int s0,
                                               int x0, int j, int k, int N, const real *Jj, const real *Jk,
                                               Partials<real> &p) {
@@ -179,7 +179,7 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
                 if (r == rs) cadd(p.A, accj[r]);
         }
     }
-    if (MODE & 1) {
+    if ((MODE & 1) && WB) {
         // B_jk: the element of row s at x* = min(k, s-k) belongs to this block for the rows s >= 2k of
         // the column tile holding k, and for the rows s - k in [x0, x0+TX) of the diagonal band.
         const bool col = (k >= x0 && k < x0 + TX);
@@ -200,14 +200,17 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
     }
 }
 
-template <typename real, int RS>
+// WB: also pick the B_jk elements out of the block (the field-only kernel); the sweep kernel gathers them
+// once per update instead (b_couplings).
+template <typename real, int RS, bool WB>
 __device__ __forceinline__ void process_block_dispatch(int mode, const typename vec2<real>::type *as, int c,
                                                        int s0, int x0, int j, int k, int N, const real *Jj,
                                                        const real *Jk, Partials<real> &p) {
-    if (mode == 3) process_block<real, RS, 3>(as, c, s0, x0, j, k, N, Jj, Jk, p);
-    else if (mode == 1) process_block<real, RS, 1>(as, c, s0, x0, j, k, N, Jj, Jk, p);
-    else if (mode == 2) process_block<real, RS, 2>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+    if (mode == 3) process_block<real, RS, 3, WB>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 1) process_block<real, RS, 1, WB>(as, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 2) process_block<real, RS, 2, WB>(as, c, s0, x0, j, k, N, Jj, Jk, p);
 }
+
 
 // Block ranges of an update: union of the runs of j and k in the sample's block list.
 struct Ranges {
@@ -225,6 +228,27 @@ __device__ __forceinline__ Ranges update_ranges(const SampleDev &sd, const int *
     R.jg = sd.J_off + mode_blk[j];
     R.kg = sd.J_off + mode_blk[k];
     return R;
+}
+
+// Smallest N for which the sweep kernel gathers the B_jk couplings once per update (b_coupling) instead of
+// picking them out of the blocks (measured on GB300: faster from N = 128 on, slower at N = 16 and 64).
+constexpr int kGatherBMinN = 96;
+// ... compiled into the FP32 shapes of 8 chains per block only (the large-N shapes); the others keep no trace
+// of it (their per-update work is too small to hide any fixed cost)
+template <typename real, int G> constexpr bool kGatherB = sizeof(real) == 4 && G == 8;
+
+// The coupling J_j[s][{k, s-k}] of quadruplet {j, s-j, k, s-k} (0 where the store holds no such entry):
+// column x* = min(k, s-k) of row s in mode j's run, read from global memory (L2-resident: the run is
+// being streamed for the same update).
+template <typename real>
+__device__ __forceinline__ real b_coupling(const real *__restrict__ J, const int *s_bo, const int *s_xtlo,
+                                           const Ranges &Rg, int s, int k) {
+    const int y = s - k, x = y < k ? y : k;
+    const int st = s / TS, xt = x / TX;
+    const int xi = xt - s_xtlo[st];
+    if (xi < 0 || xi >= s_bo[st + 1] - s_bo[st]) return real(0);
+    const int64_t gb = Rg.jg + (s_bo[st] + xi - Rg.jlo);
+    return __ldg(J + gb * JStride<real>::value + (x - xt * TX) * TS + (s - st * TS));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -312,11 +336,15 @@ template <typename real, int G, int NCW> struct SweepShape {
     static constexpr int WPW = 32 / G;
     static constexpr int NW = NCW * WPW;
     static constexpr int CB = NW;
-    static constexpr int NST = 3;
     static constexpr int RS = RowStride<real, G>::value;
     static constexpr int NTHREADS = (NCW + 1) * 32;
     static constexpr int JS = JStride<real>::value;
     static constexpr size_t stage_bytes = (size_t)2 * CB * JS * sizeof(real);
+    // ring depth: as many stages (3..6) as fit next to an N = 256 amplitude table in ~210 KB, so that the
+    // copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs)
+    static constexpr size_t amp_bytes_256 = (size_t)(256 + 2 * APAD) * RS * 2 * sizeof(real);
+    static constexpr int NST_FIT = (int)((210 * 1024 - amp_bytes_256 - 8 * 1024) / stage_bytes);
+    static constexpr int NST = NST_FIT < 3 ? 3 : (NST_FIT > 6 ? 6 : NST_FIT);
 };
 
 template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
@@ -339,7 +367,8 @@ template <typename real, int G, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams prm) {
     using Sh = SweepShape<real, G, NCW>;
     using V = typename vec2<real>::type;
-    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS;
+    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS, NW = Sh::NW;
+    constexpr int BT = (256 + NW - 1) / NW < 8 ? (256 + NW - 1) / NW : 8;  // B couplings held per lane
     constexpr int NCT = NCW * 32;  // consumer threads
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -499,6 +528,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             // ---------------- consumer warps
             const int *mode_blk = prm.mode_blk + sd.mode_off;
             const uint32_t *binfo = prm.blkinfo + sd.blk_off;
+            const bool gatherB = kGatherB<real, G> && N >= kGatherBMinN;
             const real cc = (real)prm.cc;
             for (int sw = sw0; sw < sw1; ++sw) {
                 const uint32_t sweep = (uint32_t)(sweep_base + sw);
@@ -514,6 +544,20 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     }
                     Partials<real> pr;
                     pr.zero();
+                    // B_jk = sum_s conj(a_{s-j}) J_j[s][{k, s-k}] a_{s-k} over s in [max(j,k), min(j,k)+N): the
+                    // couplings are loaded here (one per worker and BT-slot, shared by its chains) and used after
+                    // the chunk loop, so their latency hides behind it
+                    // (large N only: for small N the per-update gather costs more than picking the elements out
+                    // of the blocks, which process_block then does)
+                    const int sB0 = max(j, k), sB1 = gatherB ? min(j, k) + N : sB0;
+                    real bcp[BT];
+                    if (kGatherB<real, G>) {
+#pragma unroll
+                        for (int m = 0; m < BT; ++m) {
+                            const int sb = sB0 + worker + m * NW;
+                            bcp[m] = sb < sB1 ? b_coupling<real>(J, s_bo, s_xtlo, Rg, sb, k) : real(0);
+                        }
+                    }
                     for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q) {
                         const int stage = q % NST;
                         const uint32_t ph = (q / NST) & 1u;
@@ -525,10 +569,21 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
                             const real *st_j = ring + (size_t)stage * 2 * CB * JS + (size_t)worker * JS;
                             const real *st_k = st_j + (size_t)CB * JS;
-                            process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                            if (gatherB) process_block_dispatch<real, RS, false>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                            else process_block_dispatch<real, RS, true>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&empty[stage]);
+                    }
+                    if (kGatherB<real, G>) {
+#pragma unroll
+                        for (int m = 0; m < BT; ++m) {
+                            const int sb = sB0 + worker + m * NW;
+                            if (sb < sB1) caxpy(pr.B, bcp[m], cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
+                        }
+                        for (int sb = sB0 + worker + BT * NW; sb < sB1; sb += NW)  // N > BT * NW only
+                            caxpy(pr.B, b_coupling<real>(J, s_bo, s_xtlo, Rg, sb, k),
+                                  cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
                     }
                     // reduce over the workers of this warp, then across warps through shared memory
                     real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
@@ -536,10 +591,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     for (int o = G; o < 32; o <<= 1)
 #pragma unroll
                         for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+                    // layout [e][warp][chain]: the 8 chains of one (e, warp) are consecutive words, so both the
+                    // stores below and the reads after the barrier (32 lanes = 4 warps x 8 chains) are free of
+                    // bank conflicts
                     real *rb = red + (size_t)red_par * NCW * G * 8;
                     if (wq == 0) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) rb[(warp * G + c) * 8 + e] = v[e];
+                        for (int e = 0; e < 8; ++e) rb[(e * NCW + warp) * G + c] = v[e];
                     }
                     named_bar(1, NCT);
                     {
@@ -552,7 +610,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const int w = w0 + wq;
                             if (w < NCW) {
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) t[e] += rb[(w * G + c) * 8 + e];
+                                for (int e = 0; e < 8; ++e) t[e] += rb[(e * NCW + w) * G + c];
                             }
                         }
                         __syncwarp();
@@ -662,7 +720,7 @@ __global__ void fields_kernel(FieldsParams prm) {
         const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
         const real *Jj = J + (Rg.jg + (b - Rg.jlo)) * JStride<real>::value;
         const real *Jk = J + (Rg.kg + (b - Rg.klo)) * JStride<real>::value;
-        process_block_dispatch<real, RS>(mode, as, c, st * TS, xt * TX, j, k, N, Jj, Jk, pr);
+        process_block_dispatch<real, RS, true>(mode, as, c, st * TS, xt * TX, j, k, N, Jj, Jk, pr);
     }
     real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
 #pragma unroll
