@@ -690,7 +690,7 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
     // ---- scheduling shape
     const int chains_ps = replicas * n_T;
     // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
-    // N >= 128: 8 chains x 12 warps; 48 <= N < 128: 32 x 7 when a sample has >= 32 chains; else 16 x 7
+    // N >= 128: 8 chains x 11 warps; 48 <= N < 128: 32 x 7 when a sample has >= 32 chains; else 16 x 7
     int G = cfg.chains_per_block, ncw = 0;
     if (G == 0) {
         if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
@@ -700,7 +700,7 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
         if (G > 8 && chains_ps <= 8) G = 8;
     }
     if (c->dbl) ncw = (G == 16) ? 3 : 7;
-    else ncw = (G == 8) ? (c->maxN >= 128 ? 12 : 7) : 7;
+    else ncw = (G == 8) ? (c->maxN >= 128 ? 11 : 7) : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;

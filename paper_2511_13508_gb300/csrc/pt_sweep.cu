@@ -200,6 +200,141 @@ __device__ __forceinline__ void process_block(const typename vec2<real>::type *_
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Packed-FP32 block arithmetic (the FP32 shapes of 8 chains per block).  Rows are taken in pairs (r, r+1)
+// and every quantity is a float2 pair over the two rows, so each instruction is an FFMA2/FMUL2 doing two
+// fused multiply-adds: with
+//     sx = (Re a_x, Re a_x), sy = (Im a_x, Im a_x)                  (splats of a_x in registers)
+//     WX = (Re a_y, Re a_{y+1}), WY = (Im a_y, Im a_{y+1})          (window table awin, y = s - x)
+// the pair products of rows (s, s+1) at column x are
+//     Re z = sx WX - sy WY,   Im z = sx WY + sy WX,
+// and a field row pair accumulates acc += (J[s][x], J[s+1][x]) z with the column-major J block supplying
+// the coupling pair directly.  Two FMUL2 + two FFMA2 make 2 products; one FFMA2 per field per component
+// accumulates them: 2 instructions per coupling term when both fields use the block, 3 otherwise.
+struct PartialsX2 {
+    float2 hjx, hjy, hjyn, hkx, hky, hkyn;  // h = (hx.0 + hx.1, (hy.0 + hy.1) - (hyn.0 + hyn.1))
+    float2 B, A;
+    __device__ __forceinline__ void zero() {
+        hjx = hjy = hjyn = hkx = hky = hkyn = B = A = make_float2(0.f, 0.f);
+    }
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int G, int MODE, bool WB>
+__device__ __forceinline__ void process_block_x2(const float2 *__restrict__ as, const float4 *__restrict__ awin,
+                                                 int c, int s0, int x0, int j, int k, int N, const float *Jj,
+                                                 const float *Jk, PartialsX2 &p) {
+    constexpr int RS = RowStride<float, G>::value;
+    // Column i = 2h + pi pairs rows (2q, 2q+1) with the window starting at y-offset d = 2q - i + 7, of parity
+    // 1 - pi: the columns run in two passes by parity, each holding the 7 windows of its parity
+    // (d = 2m + 1 - pi, m = q - h + 3), so that only 7 windows are live at a time.
+    const int ybase = s0 - x0 - (TX - 1) + APAD;
+    float2 ajx[TS / 2], ajy[TS / 2], akx[TS / 2], aky[TS / 2];
+#pragma unroll
+    for (int q = 0; q < TS / 2; ++q) ajx[q] = ajy[q] = akx[q] = aky[q] = f2(0.f, 0.f);
+#pragma unroll
+    for (int pi = 0; pi < 2; ++pi) {
+        float2 wx[7], wy[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            const float4 w = awin[(ybase + 2 * m + 1 - pi) * G + c];
+            wx[m] = f2(w.x, w.y);
+            wy[m] = f2(w.z, w.w);
+        }
+#pragma unroll
+        for (int h = 0; h < TX / 2; ++h) {
+            const int i = 2 * h + pi;
+            // splats of a_x in registers (register moves cost less than the shared-memory bandwidth of a table)
+            const float2 axv = as[(x0 + i + APAD) * RS + c];
+            const float2 sx = f2(axv.x, axv.x), sy = f2(axv.y, axv.y), nsy = f2(-axv.y, -axv.y);
+            float2 jp[TS / 2], kp[TS / 2];
+            if (MODE & 1) {
+                const float4 a = *reinterpret_cast<const float4 *>(Jj + i * TS), b = *reinterpret_cast<const float4 *>(Jj + i * TS + 4);
+                jp[0] = f2(a.x, a.y); jp[1] = f2(a.z, a.w); jp[2] = f2(b.x, b.y); jp[3] = f2(b.z, b.w);
+            }
+            if (MODE & 2) {
+                const float4 a = *reinterpret_cast<const float4 *>(Jk + i * TS), b = *reinterpret_cast<const float4 *>(Jk + i * TS + 4);
+                kp[0] = f2(a.x, a.y); kp[1] = f2(a.z, a.w); kp[2] = f2(b.x, b.y); kp[3] = f2(b.z, b.w);
+            }
+#pragma unroll
+            for (int q = 0; q < TS / 2; ++q) {
+                const int m = q - h + 3;
+                const float2 zx = __ffma2_rn(sx, wx[m], __fmul2_rn(nsy, wy[m]));
+                const float2 zy = __ffma2_rn(sx, wy[m], __fmul2_rn(sy, wx[m]));
+                if (MODE & 1) { ajx[q] = __ffma2_rn(jp[q], zx, ajx[q]); ajy[q] = __ffma2_rn(jp[q], zy, ajy[q]); }
+                if (MODE & 2) { akx[q] = __ffma2_rn(kp[q], zx, akx[q]); aky[q] = __ffma2_rn(kp[q], zy, aky[q]); }
+            }
+        }
+    }
+    // close the rows: h += conj(m) acc with m = a_{s-l} for the row pair (s, s+1) from the window table
+#pragma unroll
+    for (int q = 0; q < TS / 2; ++q) {
+        if (MODE & 1) {
+            const float4 w = awin[(s0 + 2 * q - j + APAD) * G + c];
+            const float2 mx = f2(w.x, w.y), my = f2(w.z, w.w);
+            p.hjx = __ffma2_rn(mx, ajx[q], p.hjx);
+            p.hjx = __ffma2_rn(my, ajy[q], p.hjx);
+            p.hjy = __ffma2_rn(mx, ajy[q], p.hjy);
+            p.hjyn = __ffma2_rn(my, ajx[q], p.hjyn);
+        }
+        if (MODE & 2) {
+            const float4 w = awin[(s0 + 2 * q - k + APAD) * G + c];
+            const float2 mx = f2(w.x, w.y), my = f2(w.z, w.w);
+            p.hkx = __ffma2_rn(mx, akx[q], p.hkx);
+            p.hkx = __ffma2_rn(my, aky[q], p.hkx);
+            p.hky = __ffma2_rn(mx, aky[q], p.hky);
+            p.hkyn = __ffma2_rn(my, akx[q], p.hkyn);
+        }
+    }
+    if (MODE & 1) {
+        // A_jk is the accumulator of row j+k
+        const int rs = j + k - s0;
+        if (rs >= 0 && rs < TS) {
+#pragma unroll
+            for (int q = 0; q < TS / 2; ++q) {
+                if (rs == 2 * q) { p.A.x += ajx[q].x; p.A.y += ajy[q].x; }
+                if (rs == 2 * q + 1) { p.A.x += ajx[q].y; p.A.y += ajy[q].y; }
+            }
+        }
+    }
+    if ((MODE & 1) && WB) {
+        const bool col = (k >= x0 && k < x0 + TX);
+        const bool diag = (s0 + TS - 1 >= x0 + k) && (s0 <= x0 + TX - 1 + k);
+        if (col || diag) {
+#pragma unroll
+            for (int r = 0; r < TS; ++r) {
+                const int s = s0 + r, y = s - k;
+                const int xs = (y < k) ? y : k;
+                if (y >= 0 && y < N && xs >= x0 && xs < x0 + TX) {
+                    const float Jv = Jj[(xs - x0) * TS + r];
+                    const float2 m = as[(s - j + APAD) * RS + c];
+                    const float2 yv = as[(y + APAD) * RS + c];
+                    caxpy(p.B, Jv, cmulc(m, yv));
+                }
+            }
+        }
+    }
+}
+
+template <int G, bool WB>
+__device__ __forceinline__ void process_block_x2_dispatch(int mode, const float2 *as, const float4 *awin, int c,
+                                                          int s0, int x0, int j, int k, int N, const float *Jj,
+                                                          const float *Jk, PartialsX2 &p) {
+    if (mode == 3) process_block_x2<G, 3, WB>(as, awin, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 1) process_block_x2<G, 1, WB>(as, awin, c, s0, x0, j, k, N, Jj, Jk, p);
+    else if (mode == 2) process_block_x2<G, 2, WB>(as, awin, c, s0, x0, j, k, N, Jj, Jk, p);
+}
+
+// Window entry of one amplitude-table row (shared-memory row index R = x + APAD): (Re a_R, Re a_{R+1},
+// Im a_R, Im a_{R+1}).
+template <int RS>
+__device__ __forceinline__ void packed_rows(const float2 *as, float4 *awin, int G, int R, int rows, int c) {
+    const float2 a = as[R * RS + c];
+    const float2 b = (R + 1 < rows) ? as[(R + 1) * RS + c] : make_float2(0.f, 0.f);
+    awin[R * G + c] = make_float4(a.x, b.x, a.y, b.y);
+}
+
 // WB: also pick the B_jk elements out of the block (the field-only kernel); the sweep kernel gathers them
 // once per update instead (b_couplings).
 template <typename real, int RS, bool WB>
@@ -342,7 +477,9 @@ template <typename real, int G, int NCW> struct SweepShape {
     static constexpr size_t stage_bytes = (size_t)2 * CB * JS * sizeof(real);
     // ring depth: as many stages (3..6) as fit next to an N = 256 amplitude table in ~210 KB, so that the
     // copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs)
-    static constexpr size_t amp_bytes_256 = (size_t)(256 + 2 * APAD) * RS * 2 * sizeof(real);
+    static constexpr bool PACKED = sizeof(real) == 4 && G == 8;  // packed-FP32 block arithmetic
+    static constexpr size_t amp_bytes_256 = (size_t)(256 + 2 * APAD) * RS * 2 * sizeof(real) +
+                                            (PACKED ? (size_t)(256 + 2 * APAD) * G * sizeof(float4) : 0);
     static constexpr int NST_FIT = (int)((210 * 1024 - amp_bytes_256 - 8 * 1024) / stage_bytes);
     static constexpr int NST = NST_FIT < 3 ? 3 : (NST_FIT > 6 ? 6 : NST_FIT);
 };
@@ -355,6 +492,7 @@ template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
     b = (b + 127) / 128 * 128;
     b += Sh::NST * Sh::stage_bytes;                                       // J ring
     b += (size_t)(maxN + 2 * APAD) * Sh::RS * sizeof(V);                  // amplitudes
+    if (Sh::PACKED) b += (size_t)(maxN + 2 * APAD) * G * sizeof(float4);      // window table
     b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
     b += (size_t)2 * G * sizeof(Proposal<real>) + 16;                     // proposals, double-buffered
     b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
@@ -379,6 +517,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     off += NST * Sh::stage_bytes;
     V *as = reinterpret_cast<V *>(smem + off);
     off += (size_t)(prm.maxN + 2 * APAD) * RS * sizeof(V);
+    float4 *awin = nullptr;
+    if (Sh::PACKED) {
+        awin = reinterpret_cast<float4 *>(smem + off);
+        off += (size_t)(prm.maxN + 2 * APAD) * G * sizeof(float4);
+    }
     real *red = reinterpret_cast<real *>(smem + off);
     off += (size_t)2 * NCW * G * 8 * sizeof(real);
     off = (off + 15) / 16 * 16;
@@ -490,6 +633,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                 as[(x + APAD) * RS + cc] = v;
             }
             named_bar(1, NCT);
+            if (Sh::PACKED) {
+                for (int i = tid; i < rows * G; i += NCT)
+                    packed_rows<RS>(reinterpret_cast<const float2 *>(as), awin, G, i / G, rows, i % G);
+                named_bar(1, NCT);
+            }
         }
 
         if (producer) {
@@ -544,6 +692,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     }
                     Partials<real> pr;
                     pr.zero();
+                    PartialsX2 prx;
+                    prx.zero();
                     // B_jk = sum_s conj(a_{s-j}) J_j[s][{k, s-k}] a_{s-k} over s in [max(j,k), min(j,k)+N): the
                     // couplings are loaded here (one per worker and BT-slot, shared by its chains) and used after
                     // the chunk loop, so their latency hides behind it
@@ -569,11 +719,26 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
                             const real *st_j = ring + (size_t)stage * 2 * CB * JS + (size_t)worker * JS;
                             const real *st_k = st_j + (size_t)CB * JS;
-                            if (gatherB) process_block_dispatch<real, RS, false>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
-                            else process_block_dispatch<real, RS, true>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                            if constexpr (Sh::PACKED) {
+                                const float2 *asf = reinterpret_cast<const float2 *>(as);
+                                const float *fj = reinterpret_cast<const float *>(st_j), *fk = reinterpret_cast<const float *>(st_k);
+                                if (gatherB) process_block_x2_dispatch<G, false>(mode, asf, awin, c, st * TS, xt * TX, j, k, N, fj, fk, prx);
+                                else process_block_x2_dispatch<G, true>(mode, asf, awin, c, st * TS, xt * TX, j, k, N, fj, fk, prx);
+                            } else {
+                                if (gatherB) process_block_dispatch<real, RS, false>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                                else process_block_dispatch<real, RS, true>(mode, as, c, st * TS, xt * TX, j, k, N, st_j, st_k, pr);
+                            }
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&empty[stage]);
+                    }
+                    if constexpr (Sh::PACKED) {
+                        pr.hj.x = prx.hjx.x + prx.hjx.y;
+                        pr.hj.y = (prx.hjy.x + prx.hjy.y) - (prx.hjyn.x + prx.hjyn.y);
+                        pr.hk.x = prx.hkx.x + prx.hkx.y;
+                        pr.hk.y = (prx.hky.x + prx.hky.y) - (prx.hkyn.x + prx.hkyn.y);
+                        pr.B.x = prx.B.x; pr.B.y = prx.B.y;
+                        pr.A.x = prx.A.x; pr.A.y = prx.A.y;
                     }
                     if (kGatherB<real, G>) {
 #pragma unroll
@@ -628,6 +793,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             if (acc) {
                                 as[(j + APAD) * RS + c] = P.nj;
                                 as[(k + APAD) * RS + c] = P.nk;
+                                if constexpr (Sh::PACKED) {
+                                    // every warp writes the same values, after its own writes of a_j and a_k
+                                    const float2 *asf = reinterpret_cast<const float2 *>(as);
+                                    const int rows = N + 2 * APAD;
+                                    packed_rows<RS>(asf, awin, G, j - 1 + APAD, rows, c);
+                                    packed_rows<RS>(asf, awin, G, j + APAD, rows, c);
+                                    packed_rows<RS>(asf, awin, G, k - 1 + APAD, rows, c);
+                                    packed_rows<RS>(asf, awin, G, k + APAD, rows, c);
+                                }
                             }
                             if (warp == 0 && c < gr.count) {
                                 if (acc) { cE[c] += (double)dH; cAcc[c] += 1u; }
