@@ -157,6 +157,28 @@ def cpu_oracle_rate(target_seconds=CPU_SAMPLE_SECONDS, workers=None):
                       % (workers, len(temps), sweeps)}
 
 
+# ------------------------------------------------------------------------------------------- ranks
+def rank_seeds(seeds, rank):
+    """Weak scaling: every rank simulates its own disorder samples (seed ranges 1000 apart); samples are
+    independent problems, so the data path needs no collective."""
+    return [int(s) + 1000 * int(rank) for s in seeds]
+
+
+def max_over_ranks(value, dist, device="cpu"):
+    """The timing rule: the slowest rank's time (all-reduce MAX; identity on one rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 # ------------------------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, dist):
     import torch
@@ -167,7 +189,7 @@ def run_gpu(args, rank, world, dist):
     pkg.build()
     W = workload.workloads()["n256_large"]
     nq = len(pkg.enumerate_quads(N_MODES))
-    seeds = [s + 1000 * rank for s in W.seeds]  # weak scaling: every rank its own 16 samples
+    seeds = rank_seeds(W.seeds, rank)  # weak scaling: every rank its own 16 samples
     Js = [workload.couplings(N_MODES, nq, s) for s in seeds]
     stream = torch.cuda.Stream()
     kw = dict(swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
@@ -192,12 +214,8 @@ def run_gpu(args, rank, world, dist):
         barrier()
     pt.sync()
     ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_cs = chains * STEP_SWEEPS * args.steps * world
-    value = total_cs / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, device="cuda")
+    value = whole_job_rate(chains * STEP_SWEEPS * args.steps, world, ms)
 
     # ---- sweep kernel alone (roofline): one launch of 64 sweeps without measurement/resync/swap
     pk = pkg.PT(W.Ns, Js, W.temps, W.replicas, 777, precision="fp32", stream=stream, swap_every=0,
