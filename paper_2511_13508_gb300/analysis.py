@@ -1,0 +1,113 @@
+"""Host-side statistics over the engine's accumulators (arXiv 2511.13508, Sec. III.B and IV).
+
+- thermal averages per disorder sample, Eq. (totave), from the per-(sample, T) sums of `PT.observables()`;
+- disorder averages over samples, Eq. (DisAver), with leave-one-sample-out jackknife errors (Sec. III.B.3);
+- specific heat C_V = beta^2 (<E^2> - <E>^2) per sample, then averaged (Eq. (21));
+- kurtosis of the overlap, K_N(T) = mean<q^4> / (mean<q^2>)^2 (Eq. (kurt), with <q> = 0 exactly by the
+  global-phase symmetry), and the temperatures where the curves of two sizes cross;
+- thermalisation checks (Sec. III.B.1): averages over windows of doubling length, and the symmetry of the
+  per-sample overlap distribution P_J(q) = P_J(-q).
+
+Layouts: stat [S][T][7] = (n, E, E^2, Y2, Y4, I, I^2), qstat [S][T][5] = (n, q, q^2, q^3, q^4),
+qhist [S][T][201] with bin b centred at q = b/100 - 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def thermal_averages(obs: dict, temps) -> dict:
+    """Per-sample thermal averages [S, T] (Eq. (totave)) and C_V = beta^2 (<E^2> - <E>^2)."""
+    st = np.asarray(obs["stat"], np.float64)
+    qs = np.asarray(obs["qstat"], np.float64)
+    n = st[..., 0]
+    nq = np.maximum(qs[..., 0], 1.0)
+    beta = 1.0 / np.asarray(temps, np.float64)
+    E, E2 = st[..., 1] / n, st[..., 2] / n
+    return {
+        "n": n, "E": E, "E2": E2, "CV": beta[None, :] ** 2 * (E2 - E * E),
+        "Y2": st[..., 3] / n, "Y4": st[..., 4] / n, "I": st[..., 5] / n, "I2": st[..., 6] / n,
+        "q": qs[..., 1] / nq, "q2": qs[..., 2] / nq, "q4": qs[..., 4] / nq,
+    }
+
+
+def jackknife(per_sample: np.ndarray, estimator=lambda x: x.mean(0)):
+    """Leave-one-sample-out jackknife over axis 0 of `per_sample` (or of every array in a tuple):
+    returns (estimate with first-order bias removed, standard error)."""
+    arrays = per_sample if isinstance(per_sample, tuple) else (per_sample,)
+    S = arrays[0].shape[0]
+    full = np.asarray(estimator(*arrays))
+    if S < 2:
+        return full, np.full_like(full, np.nan, dtype=np.float64)
+    loo = np.stack([np.asarray(estimator(*[np.delete(a, i, axis=0) for a in arrays])) for i in range(S)])
+    mean_loo = loo.mean(0)
+    est = S * full - (S - 1) * mean_loo
+    err = np.sqrt((S - 1) / S * ((loo - mean_loo) ** 2).sum(0))
+    return est, err
+
+
+def disorder_average(per_sample: np.ndarray):
+    """Eq. (DisAver) with its jackknife error: mean over samples (axis 0)."""
+    return jackknife(np.asarray(per_sample, np.float64))
+
+
+def specific_heat(obs: dict, temps):
+    """Disorder-averaged C_V(T) per temperature and its jackknife error."""
+    return disorder_average(thermal_averages(obs, temps)["CV"])
+
+
+def kurtosis(obs: dict, temps=None):
+    """K_N(T) = mean<q^4> / (mean<q^2>)^2 over samples, with its jackknife error."""
+    ta = thermal_averages(obs, temps if temps is not None else np.ones(np.asarray(obs["stat"]).shape[1]))
+    return jackknife((ta["q4"], ta["q2"]), lambda q4, q2: q4.mean(0) / q2.mean(0) ** 2)
+
+
+def crossings(T, K1, K2):
+    """Temperatures where K1(T) - K2(T) changes sign, by linear interpolation between ladder points."""
+    T = np.asarray(T, np.float64)
+    d = np.asarray(K1, np.float64) - np.asarray(K2, np.float64)
+    out = []
+    for i in range(len(T) - 1):
+        if d[i] == 0.0:
+            out.append(T[i])
+        elif d[i] * d[i + 1] < 0.0:
+            out.append(T[i] - d[i] * (T[i + 1] - T[i]) / (d[i + 1] - d[i]))
+    if len(d) and d[-1] == 0.0:
+        out.append(T[-1])
+    return np.asarray(out)
+
+
+def pq_symmetry(qhist: np.ndarray, min_count: int = 5) -> np.ndarray:
+    """Chi-square per degree of freedom of P_J(q) against P_J(-q), per (sample, T): bins b and 200 - b
+    (b < 100) with at least `min_count` entries together; about 1 for a symmetric distribution.
+    NaN where no pair of bins is populated.  (Counts of one run are correlated in time, so a value
+    somewhat above 1 is expected for short runs; a broken symmetry gives values far above.)"""
+    h = np.asarray(qhist, np.float64)
+    a, b = h[..., :100], h[..., 200:100:-1]
+    tot = a + b
+    use = tot >= min_count
+    chi = np.where(use, (a - b) ** 2 / np.where(use, tot, 1.0), 0.0).sum(-1)
+    dof = use.sum(-1)
+    return np.where(dof > 0, chi / np.maximum(dof, 1), np.nan)
+
+
+def doubling_windows(pt, n_windows: int, first: int = 1):
+    """Runs windows of first, 2 first, 4 first, ... sweeps (Sec. III.B.1) and returns the observables of
+    each window (accumulators reset at every window start)."""
+    out = []
+    length = int(first)
+    for _ in range(int(n_windows)):
+        pt.reset_observables()
+        pt.sweep(length)
+        out.append(pt.observables())
+        length *= 2
+    return out
+
+
+def thermalised(windows, temps, key: str = "E", z: float = 3.0) -> np.ndarray:
+    """Per temperature: True where the disorder averages of `key` over the last two doubling windows agree
+    within z jackknife errors of their difference (paired over samples)."""
+    a = thermal_averages(windows[-2], temps)[key]
+    b = thermal_averages(windows[-1], temps)[key]
+    d, err = jackknife(b - a)
+    return np.abs(d) <= z * err + 1e-12

@@ -257,13 +257,23 @@ __device__ __forceinline__ void process_block_x2(const float2 *__restrict__ as, 
                 const float4 a = *reinterpret_cast<const float4 *>(Jk + i * TS), b = *reinterpret_cast<const float4 *>(Jk + i * TS + 4);
                 kp[0] = f2(a.x, a.y); kp[1] = f2(a.z, a.w); kp[2] = f2(b.x, b.y); kp[3] = f2(b.z, b.w);
             }
+            float2 tx[TS / 2], ty[TS / 2], zx[TS / 2], zy[TS / 2];
 #pragma unroll
             for (int q = 0; q < TS / 2; ++q) {
                 const int m = q - h + 3;
-                const float2 zx = __ffma2_rn(sx, wx[m], __fmul2_rn(nsy, wy[m]));
-                const float2 zy = __ffma2_rn(sx, wy[m], __fmul2_rn(sy, wx[m]));
-                if (MODE & 1) { ajx[q] = __ffma2_rn(jp[q], zx, ajx[q]); ajy[q] = __ffma2_rn(jp[q], zy, ajy[q]); }
-                if (MODE & 2) { akx[q] = __ffma2_rn(kp[q], zx, akx[q]); aky[q] = __ffma2_rn(kp[q], zy, aky[q]); }
+                tx[q] = __fmul2_rn(nsy, wy[m]);
+                ty[q] = __fmul2_rn(sy, wx[m]);
+            }
+#pragma unroll
+            for (int q = 0; q < TS / 2; ++q) {
+                const int m = q - h + 3;
+                zx[q] = __ffma2_rn(sx, wx[m], tx[q]);
+                zy[q] = __ffma2_rn(sx, wy[m], ty[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < TS / 2; ++q) {
+                if (MODE & 1) { ajx[q] = __ffma2_rn(jp[q], zx[q], ajx[q]); ajy[q] = __ffma2_rn(jp[q], zy[q], ajy[q]); }
+                if (MODE & 2) { akx[q] = __ffma2_rn(kp[q], zx[q], akx[q]); aky[q] = __ffma2_rn(kp[q], zy[q], aky[q]); }
             }
         }
     }

@@ -1,0 +1,99 @@
+"""Pins of the host-side statistics (Sec. III.B, IV) against closed forms, and of the kurtosis of the
+overlap against its exact beta = 0 value on oracle runs."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle
+from paper_2511_13508_gb300 import analysis, workload
+
+
+def test_jackknife_of_a_mean_is_the_standard_error():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((40, 3)) * [1.0, 2.0, 0.5] + [0.0, 1.0, -2.0]
+    est, err = analysis.jackknife(x)
+    assert np.allclose(est, x.mean(0), rtol=0, atol=1e-12)
+    assert np.allclose(err, x.std(0, ddof=1) / math.sqrt(len(x)), rtol=1e-12)
+
+
+def test_jackknife_removes_the_bias_of_a_squared_mean():
+    """For theta = mean(x)^2 the jackknife estimate is mean^2 - s^2/n exactly (s^2 unbiased variance)."""
+    rng = np.random.default_rng(2)
+    x = rng.normal(0.3, 1.0, 25)
+    est, _ = analysis.jackknife(x, lambda v: v.mean(0) ** 2)
+    assert abs(est - (x.mean() ** 2 - x.var(ddof=1) / len(x))) < 1e-12
+
+
+def _qstat_from_samples(q):
+    """Accumulators of one (sample, T) cell from overlap values."""
+    return np.array([len(q), q.sum(), (q ** 2).sum(), (q ** 3).sum(), (q ** 4).sum()])
+
+
+def test_kurtosis_of_gaussian_and_two_point_overlaps():
+    rng = np.random.default_rng(3)
+    S, T = 16, 2
+    stat = np.ones((S, T, 7))
+    qg = np.stack([np.stack([_qstat_from_samples(rng.normal(0, 0.2, 20000)) for _ in range(T)]) for _ in range(S)])
+    K, dK = analysis.kurtosis({"stat": stat, "qstat": qg})
+    assert np.all(np.abs(K - 3.0) < 4 * dK + 0.02)
+    q2 = np.stack([np.stack([_qstat_from_samples(rng.choice([-0.4, 0.4], 1000)) for _ in range(T)]) for _ in range(S)])
+    K2, dK2 = analysis.kurtosis({"stat": stat, "qstat": q2})
+    assert np.allclose(K2, 1.0, atol=1e-12) and np.all(dK2 < 1e-12)
+
+
+def test_crossings_of_straight_lines():
+    T = np.linspace(0.2, 1.0, 9)
+    K1 = 2.0 + 3.0 * (T - 0.43)
+    K2 = 2.0 - 1.0 * (T - 0.43)
+    c = analysis.crossings(T, K1, K2)
+    assert len(c) == 1 and abs(c[0] - 0.43) < 1e-12
+    assert len(analysis.crossings(T, K1, K1 + 1.0)) == 0
+
+
+def test_pq_symmetry_separates_symmetric_and_shifted_histograms():
+    rng = np.random.default_rng(4)
+    centres = np.arange(201) / 100 - 1
+    p = np.exp(-centres ** 2 / (2 * 0.15 ** 2)); p /= p.sum()
+    sym = rng.multinomial(200000, p, size=(3, 2))
+    ps = np.exp(-(centres - 0.05) ** 2 / (2 * 0.15 ** 2)); ps /= ps.sum()
+    shifted = rng.multinomial(200000, ps, size=(3, 2))
+    assert np.all(analysis.pq_symmetry(sym) < 1.6)
+    assert np.all(analysis.pq_symmetry(shifted) > 10.0)
+
+
+def kurtosis_beta0(N):
+    """Exact kurtosis of q = Re sum_k conj(a_k) b_k / N for two independent draws of the beta = 0 law of
+    Eq. (8): intensities s = |a|^4/N ~ Dirichlet(1/2) (so E|a_k|^4 = 1, E|a_k|^2|a_l|^2 = 2/pi for k != l)
+    and independent uniform phases (E cos^2 = 1/2, E cos^4 = 3/8)."""
+    Eq2 = special.gamma(N / 2) ** 2 / (2 * math.pi * special.gamma((N + 1) / 2) ** 2)
+    Eq4 = (3 * N / 8 + 3 * N * (N - 1) / math.pi ** 2) / N ** 4
+    return Eq4 / Eq2 ** 2
+
+
+def test_kurtosis_at_beta0_matches_the_exact_value_on_oracle_runs():
+    N, S, R, nT = 8, 4, 8, 2
+    J0 = [np.zeros(len(oracle.enumerate_quads(N)))] * S
+    pt = oracle.OraclePT([N] * S, J0, workload.geometric_ladder(0.5, 1.0, nT), R, 5, swap_every=0,
+                         measure_every=4, resync_every=64)
+    pt.sweep(4000)
+    K, dK = analysis.kurtosis(pt.observables())
+    K0 = kurtosis_beta0(N)
+    assert abs(K0 - 3.0) > 0.2  # the finite-N value is far from the Gaussian one
+    # measurements 4 sweeps apart are correlated: allow for an integrated autocorrelation of a few
+    assert np.all(np.abs(K - K0) < 5 * dK + 0.03), (K, K0, dK)
+
+
+def test_doubling_windows_detect_relaxation_on_oracle_runs():
+    """From the beta = 0 start the coldest chains relax: the first short windows disagree, the last two
+    (thermalised) windows agree."""
+    N, S, R, nT = 8, 8, 2, 3
+    Js = [workload.couplings(N, len(oracle.enumerate_quads(N)), 30 + s) for s in range(S)]
+    temps = workload.geometric_ladder(0.15, 1.0, nT)
+    pt = oracle.OraclePT([N] * S, Js, temps, R, 6, swap_every=8, measure_every=1, resync_every=64)
+    w = analysis.doubling_windows(pt, 11, first=1)
+    assert not analysis.thermalised(w[:2], temps)[0]
+    assert np.all(analysis.thermalised(w, temps))
+    E = [analysis.disorder_average(analysis.thermal_averages(x, temps)["E"])[0][0] for x in w]
+    assert E[-1] < E[0]
