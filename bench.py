@@ -289,6 +289,34 @@ def learned_leg():
     return r
 
 
+def graph_leg(sweeps=4):
+    """The paper's own graph: random mode frequencies with the matching condition of linewidth
+    1/(2(N-1)) (N = 64, 16 samples x 32 T [0.3,1.6] x 2 replicas), on the quadruplet-list FP64 path;
+    a bounded sample of sweeps timed with CUDA events on the library's stream."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    N, S, R = 64, 16, 2
+    temps = workload.geometric_ladder(0.3, 1.6, 32)
+    graphs = [pkg.fmc_graph(workload.random_frequencies(N, 500 + s)) for s in range(S)]
+    Js = [workload.couplings(N, len(g), 600 + s) for s, g in enumerate(graphs)]
+    stream = torch.cuda.Stream()
+    pt = pkg.PT([N] * S, Js, temps, R, 31, precision="fp64_plain", stream=stream, graphs=graphs,
+                swap_every=64, measure_every=16, resync_every=64)
+    pt.sweep(1)
+    pt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pt.sweep(sweeps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    rate = pt.n_chains * sweeps / (ev0.elapsed_time(ev1) / 1e3)
+    pt.close()
+    return {"workload": "N=64 random-frequency mode-locked graph (gamma = 1/(2(N-1))), 16 samples x 32 T x 2 "
+                        "replicas, FP64 quadruplet-list path", "value": rate, "unit": "chain-sweeps/s",
+            "quadruplets_per_sample_mean": float(np.mean([len(g) for g in graphs])), "sweeps": sweeps}
+
+
 def profile_case():
     """Three launches of the sweep kernel (one sweep each) on half the bench workload: 8 samples
     (176 MB of couplings, larger than L2), 768 chains; no measurement, resync or swap."""
@@ -316,6 +344,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal ESS comparison")
+    ap.add_argument("--no-graph", action="store_true", help="skip the random-frequency graph leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     args = ap.parse_args()
@@ -360,6 +389,9 @@ def main():
     learned = None
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg()
+    graph = None
+    if rank == 0 and world == 1 and not args.no_graph:
+        graph = graph_leg()
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -376,7 +408,8 @@ def main():
                 "gpu_launches": 5 * args.steps,
                 "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
                                    "speedup_fp32": r["value"] / world / r["plain_rate"]},
-                "learned_vs_plain": learned}
+                "learned_vs_plain": learned,
+                "random_graph": graph}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -118,6 +118,28 @@ int pt_create(pt_ctx **out, const pt_config *cfg, int S, const int32_t *N, const
               const int64_t *J_offsets, int n_T, const double *temps, int replicas, uint64_t seed,
               pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);
 
+/* Random-frequency mode-locked graph (paper Sec. II.C "Quenched random frequencies" and "Graph generation",
+ * Eq. (1) with the linewidth of Eq. (gamma_scaling), gamma = 1/(2(N-1)) for frequencies in [0,1]).
+ *  omega  [N] mode frequencies, strictly ascending (the modes are indexed in frequency order).
+ *  gamma  linewidth of the matching condition, > 0.
+ * For every 4-subset a<b<c<d, each of its three splittings into a conjugated pair {p,q} and a plain
+ * pair {u,v} with |omega_p + omega_q - omega_u - omega_v| < gamma is one interaction with its own
+ * coupling; it is written as (p, u, v, q) so that its term of H is -cc J Re(conj(a_p) a_u a_v conj(a_q)).
+ * Order: by (a, b, c, d), then splitting {a,d}|{b,c}, {a,b}|{c,d}, {a,c}|{b,d}.  With omega_k = k/(N-1)
+ * the list is exactly that of pt_enumerate_quads.  Writes 4*count int32 to quads when quads != NULL.
+ * PT_EINVAL for N outside 4..512, a non-ascending omega, gamma <= 0 or count == NULL.  Host code. */
+int pt_fmc_graph(int N, const double *omega, double gamma, int32_t *quads, int64_t *count);
+
+/* As pt_create, on explicit interaction lists instead of the comb: sample s has the quadruplets
+ * quads[4 q_offsets[s] .. 4 q_offsets[s+1]) in term order (term -cc J Re(conj(a_q0) a_q1 a_q2 conj(a_q3)),
+ * the four modes distinct and < N[s]) and the couplings J[q_offsets[s] .. q_offsets[s+1]) (q_offsets[0] = 0).
+ * Runs on the quadruplet-list path: cfg->precision must be PT_PREC_FP64_PLAIN (PT_EUNSUPPORTED otherwise);
+ * pt_fields and pt_autotune are unsupported there, as for that path on the comb.  PT_EINVAL for a bad
+ * index or offsets.  The caller keeps ownership of the arrays. */
+int pt_create_graph(pt_ctx **out, const pt_config *cfg, int S, const int32_t *N, const int32_t *quads,
+                    const double *J, const int64_t *q_offsets, int n_T, const double *temps, int replicas,
+                    uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);
+
 /* Runs n_sweeps Monte Carlo sweeps (one sweep = N/2 pair updates per chain, Sec. III.A.1) on every
  * chain, asynchronously.  After each completed sweep t (counted from creation) the schedule is:
  * resync if t % resync_every == 0, measure if t % measure_every == 0, swap pass if

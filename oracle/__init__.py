@@ -63,6 +63,10 @@ def lib() -> ctypes.CDLL:
         L.or_pt_create.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, c_u64, c_d,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_pt_create.restype = vp
+        L.or_pt_create_graph.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, c_u64, c_d,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_pt_create_graph.restype = vp
+        L.or_fmc_graph.argtypes = [ctypes.c_int, vp, c_d, vp]; L.or_fmc_graph.restype = c_i64
         L.or_pt_destroy.argtypes = [vp]
         L.or_pt_sweep.argtypes = [vp, c_i64]
         L.or_pt_swap.argtypes = [vp]
@@ -88,6 +92,18 @@ def philox(ctr, key):
     o = (ctypes.c_uint32 * 4)()
     lib().or_philox4x32_10(c, k, o)
     return [int(v) for v in o]
+
+
+def fmc_graph(omega, gamma=None) -> np.ndarray:
+    """Random-frequency mode-locked graph by brute force (reading R10): quadruplets in term order,
+    [n, 4] int32.  omega sorted ascending; gamma defaults to 1/(2(N-1)) (Eq. (gamma_scaling))."""
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    N = len(omega)
+    g = 1.0 / (2 * (N - 1)) if gamma is None else float(gamma)
+    n = lib().or_fmc_graph(N, _p(omega), g, None)
+    out = np.zeros((max(n, 1), 4), dtype=np.int32)
+    lib().or_fmc_graph(N, _p(omega), g, _p(out))
+    return out[:n]
 
 
 def enumerate_quads(N: int) -> np.ndarray:
@@ -155,7 +171,10 @@ def qbin(q: float) -> int:
 class OraclePT:
     """Configuration-swapping FP64 Parallel Tempering over S samples x R replicas x nT temperatures."""
 
-    def __init__(self, Ns, J_list, temps, R, seed, cc=2.0, swap_every=64, measure_every=16, resync_every=64):
+    def __init__(self, Ns, J_list, temps, R, seed, cc=2.0, swap_every=64, measure_every=16, resync_every=64,
+                 graphs=None):
+        """graphs: None for the comb graph of every sample, else one [n_s, 4] quadruplet list (term order)
+        per sample, with len(J_list[s]) == n_s."""
         L = lib()
         self.Ns = np.ascontiguousarray(Ns, dtype=np.int32)
         self.S = len(self.Ns); self.R = int(R); self.temps = np.ascontiguousarray(temps, dtype=np.float64)
@@ -164,8 +183,17 @@ class OraclePT:
                                       if len(J_list) else np.zeros(0))
         self.J_off = np.zeros(self.S + 1, dtype=np.int64)
         self.J_off[1:] = np.cumsum([len(j) for j in J_list])
-        self._h = L.or_pt_create(self.S, _p(self.Ns), _p(self.J), _p(self.J_off), self.nT, _p(self.temps),
-                                 self.R, int(seed), float(cc), int(swap_every), int(measure_every), int(resync_every))
+        if graphs is None:
+            self._h = L.or_pt_create(self.S, _p(self.Ns), _p(self.J), _p(self.J_off), self.nT, _p(self.temps),
+                                     self.R, int(seed), float(cc), int(swap_every), int(measure_every),
+                                     int(resync_every))
+        else:
+            gq = [np.asarray(g, dtype=np.int32).reshape(-1, 4) for g in graphs]
+            assert [len(g) for g in gq] == [len(j) for j in J_list], "one coupling per quadruplet"
+            self.graph = np.ascontiguousarray(np.concatenate(gq) if gq else np.zeros((0, 4), np.int32))
+            self._h = L.or_pt_create_graph(self.S, _p(self.Ns), _p(self.graph), _p(self.J), _p(self.J_off), self.nT,
+                                           _p(self.temps), self.R, int(seed), float(cc), int(swap_every),
+                                           int(measure_every), int(resync_every))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -38,6 +38,12 @@
  *   R7 swaps are proposed in ascending temperature order, index 0 = coldest.
  *   R8 the overlap histogram has 201 bins centred at -1, -0.99, ..., 1; bin = floor(100(q+1)+0.5).
  *   R9 every resync_every sweeps: a <- a (N / sum|a|^4)^(1/4), then E <- H(a).
+ *   R10 random-frequency graph (Sec. II.C "Quenched random frequencies", "Graph generation",
+ *      Eq. (gamma_scaling)): sorted frequencies omega_0 < ... < omega_{N-1} in [0,1]; for every
+ *      4-subset a<b<c<d each of its three splittings into a conjugated pair {p,q} and a plain pair
+ *      {u,v} with |omega_p + omega_q - omega_u - omega_v| < gamma is one interaction with its own
+ *      coupling, stored as (p, u, v, q) so that the term is Re(conj(a_p) a_u a_v conj(a_q)); the
+ *      splittings in order: {a,d}|{b,c}, {a,b}|{c,d}, {a,c}|{b,d}.  gamma = 1/(2(N-1)).
  *
  * Random-number streams (Philox4x32-10, key = (seed_lo, seed_hi), counter = 4 words):
  *   INIT     (chain, mode, 0, 1)            chain = (s*R + r)*nT + t
@@ -104,6 +110,31 @@ int64_t or_enumerate_quads(int N, int32_t *abcd) {
                 }
                 ++n;
             }
+    return n;
+}
+
+/* Random-frequency mode-locked graph (reading R10), by brute force over every 4-subset and each of
+ * its three splittings.  omega must be sorted ascending.  Returns the count; writes 4 indices per
+ * interaction in term order if quads != NULL. */
+int64_t or_fmc_graph(int N, const double *omega, double gamma, int32_t *quads) {
+    int64_t n = 0;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            for (int c = b + 1; c < N; ++c)
+                for (int d = c + 1; d < N; ++d) {
+                    /* (conjugated p, q | plain u, v) for the three splittings */
+                    const int sp[3][4] = {{a, d, b, c}, {a, b, c, d}, {a, c, b, d}};
+                    for (int t = 0; t < 3; ++t) {
+                        const int p = sp[t][0], q = sp[t][1], u = sp[t][2], v = sp[t][3];
+                        if (fabs(omega[p] + omega[q] - omega[u] - omega[v]) < gamma) {
+                            if (quads) {
+                                quads[4 * n + 0] = p; quads[4 * n + 1] = u;
+                                quads[4 * n + 2] = v; quads[4 * n + 3] = q;
+                            }
+                            ++n;
+                        }
+                    }
+                }
     return n;
 }
 
@@ -305,8 +336,28 @@ typedef struct {
 
 static int64_t slot(const or_pt *p, int s, int r, int t) { return ((int64_t)s * p->R + r) * p->nT + t; }
 
+static or_pt *pt_create_impl(int S, const int32_t *N, const int32_t *graph, const double *J, const int64_t *J_off,
+                             int nT, const double *temps, int R, uint64_t seed, double cc, int swap_every,
+                             int measure_every, int resync_every);
+
+/* Comb graph (Eq. (1) with omega_k = k) for every sample; J_off[s] .. J_off[s+1] are its couplings in the
+ * order of or_enumerate_quads. */
 or_pt *or_pt_create(int S, const int32_t *N, const double *J, const int64_t *J_off, int nT, const double *temps,
                     int R, uint64_t seed, double cc, int swap_every, int measure_every, int resync_every) {
+    return pt_create_impl(S, N, NULL, J, J_off, nT, temps, R, seed, cc, swap_every, measure_every, resync_every);
+}
+
+/* Explicit interaction lists: sample s has the quadruplets graph[4 J_off[s] .. 4 J_off[s+1]) (term order,
+ * Re(conj(a_q0) a_q1 a_q2 conj(a_q3))) with couplings J[J_off[s] .. J_off[s+1]). */
+or_pt *or_pt_create_graph(int S, const int32_t *N, const int32_t *graph, const double *J, const int64_t *J_off,
+                          int nT, const double *temps, int R, uint64_t seed, double cc, int swap_every,
+                          int measure_every, int resync_every) {
+    return pt_create_impl(S, N, graph, J, J_off, nT, temps, R, seed, cc, swap_every, measure_every, resync_every);
+}
+
+static or_pt *pt_create_impl(int S, const int32_t *N, const int32_t *graph, const double *J, const int64_t *J_off,
+                             int nT, const double *temps, int R, uint64_t seed, double cc, int swap_every,
+                             int measure_every, int resync_every) {
     or_pt *p = (or_pt *)calloc(1, sizeof(or_pt));
     p->S = S; p->R = R; p->nT = nT; p->cc = cc; p->seed = seed;
     p->swap_every = swap_every; p->measure_every = measure_every; p->resync_every = resync_every;
@@ -319,10 +370,11 @@ or_pt *or_pt_create(int S, const int32_t *N, const double *J, const int64_t *J_o
     for (int s = 0; s < S; ++s) {
         int n = N[s];
         p->N[s] = n;
-        int64_t nq = or_enumerate_quads(n, NULL);
+        int64_t nq = graph ? J_off[s + 1] - J_off[s] : or_enumerate_quads(n, NULL);
         p->nq[s] = nq;
         p->abcd[s] = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(nq > 0 ? nq : 1));
-        or_enumerate_quads(n, p->abcd[s]);
+        if (graph) memcpy(p->abcd[s], graph + 4 * J_off[s], sizeof(int32_t) * 4 * (size_t)nq);
+        else or_enumerate_quads(n, p->abcd[s]);
         p->J[s] = (double *)malloc(sizeof(double) * (size_t)(nq > 0 ? nq : 1));
         memcpy(p->J[s], J + J_off[s], sizeof(double) * (size_t)nq);
         /* incidence lists: for mode l, the quadruplets holding l, in Q order */

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["build", "lib", "PT", "enumerate_quads", "PREC", "PTError", "NSTAT", "NQSTAT", "QBINS"]
+__all__ = ["build", "lib", "PT", "enumerate_quads", "fmc_graph", "PREC", "PTError", "NSTAT", "NQSTAT", "QBINS"]
 
 PREC = {"fp32": 0, "fp64": 1, "fp64_plain": 2}
 NSTAT, NQSTAT, QBINS = 7, 5, 201
@@ -50,7 +50,7 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
            "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_gemm_bf16",
-           "pt_energy_fp64_static"]
+           "pt_energy_fp64_static", "pt_fmc_graph", "pt_create_graph"]
 
 _lib = None
 
@@ -72,6 +72,9 @@ def lib() -> ctypes.CDLL:
         L.pt_enumerate_quads.argtypes = [i, vp, ctypes.POINTER(i64)]
         L.pt_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), i, vp, vp, vp, i, vp, i, u64,
                                 ALLOC_FN, FREE_FN, vp, vp]
+        L.pt_create_graph.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), i, vp, vp, vp, vp, i, vp, i, u64,
+                                      ALLOC_FN, FREE_FN, vp, vp]
+        L.pt_fmc_graph.argtypes = [i, vp, d, vp, ctypes.POINTER(i64)]
         L.pt_sweep.argtypes = [vp, i64]
         for n in ("pt_swap", "pt_resync", "pt_measure_now", "pt_reset_observables", "pt_sync", "pt_destroy"):
             getattr(L, n).argtypes = [vp]
@@ -102,6 +105,19 @@ def lib() -> ctypes.CDLL:
 
 def _p(x: np.ndarray):
     return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def fmc_graph(omega, gamma=None) -> np.ndarray:
+    """Random-frequency mode-locked graph (pt_fmc_graph): [n, 4] int32 quadruplets in term order.
+    omega: strictly ascending frequencies; gamma defaults to 1/(2(N-1))."""
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    N = len(omega)
+    g = 1.0 / (2 * (N - 1)) if gamma is None else float(gamma)
+    n = ctypes.c_int64()
+    _check(None, lib().pt_fmc_graph(N, _p(omega), g, None, ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    _check(None, lib().pt_fmc_graph(N, _p(omega), g, _p(out), ctypes.byref(n)))
+    return out[: n.value]
 
 
 def enumerate_quads(N: int) -> np.ndarray:
@@ -142,7 +158,9 @@ class PT:
 
     def __init__(self, Ns, J_list, temps, replicas, seed, precision="fp32", cc=2.0, swap_every=64,
                  measure_every=16, resync_every=64, chains_per_block=0, sweeps_per_unit=0, blocks_per_sm=0,
-                 consumer_warps=0, use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True):
+                 consumer_warps=0, use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True, graphs=None):
+        """graphs: None for the comb graph of every sample; else one [n_s, 4] quadruplet list per sample
+        (term order, e.g. from fmc_graph) with len(J_list[s]) == n_s, on the fp64_plain path."""
         L = lib()
         self.Ns = np.ascontiguousarray(Ns, dtype=np.int32)
         self.S, self.R = len(self.Ns), int(replicas)
@@ -173,8 +191,16 @@ class PT:
         h = ctypes.c_void_p()
         af = self._alloc.alloc if self._alloc else ALLOC_FN()
         ff = self._alloc.free if self._alloc else FREE_FN()
-        rc = L.pt_create(ctypes.byref(h), ctypes.byref(cfg), self.S, _p(self.Ns), _p(J), _p(off), self.nT,
-                         _p(self.temps), self.R, ctypes.c_uint64(int(seed)), af, ff, None, s_ptr)
+        if graphs is None:
+            rc = L.pt_create(ctypes.byref(h), ctypes.byref(cfg), self.S, _p(self.Ns), _p(J), _p(off), self.nT,
+                             _p(self.temps), self.R, ctypes.c_uint64(int(seed)), af, ff, None, s_ptr)
+        else:
+            gq = [np.asarray(g, dtype=np.int32).reshape(-1, 4) for g in graphs]
+            if [len(g) for g in gq] != [len(j) for j in J_list]:
+                raise ValueError("one coupling per quadruplet")
+            Q = np.ascontiguousarray(np.concatenate(gq) if gq else np.zeros((0, 4), np.int32))
+            rc = L.pt_create_graph(ctypes.byref(h), ctypes.byref(cfg), self.S, _p(self.Ns), _p(Q), _p(J), _p(off),
+                                   self.nT, _p(self.temps), self.R, ctypes.c_uint64(int(seed)), af, ff, None, s_ptr)
         _check(None, rc)
         self._h = h
         self.n_chains = self.S * self.R * self.nT

@@ -621,9 +621,73 @@ int pt_enumerate_quads(int N, int32_t *abcd, int64_t *count) {
     return PT_OK;
 }
 
+int pt_fmc_graph(int N, const double *omega, double gamma, int32_t *quads, int64_t *count) {
+    if (!count || !omega || N < 4 || N > 512 || !(gamma > 0.0) || !std::isfinite(gamma))
+        return fail(nullptr, PT_EINVAL, "pt_fmc_graph: need 4 <= N <= 512, omega, gamma > 0 and count");
+    for (int k = 0; k < N; ++k)
+        if (!std::isfinite(omega[k]) || (k && !(omega[k] > omega[k - 1])))
+            return fail(nullptr, PT_EINVAL, "pt_fmc_graph: omega must be finite and strictly ascending");
+    // For each a < b < c the fourth mode d > c of a matching splitting has a frequency in a window of
+    // width 2 gamma: omega_b + omega_c - omega_a (splitting {a,d}|{b,c}), omega_a + omega_b - omega_c
+    // ({a,b}|{c,d}) or omega_a + omega_c - omega_b ({a,c}|{b,d}); the windows are found by binary search
+    // and the candidates kept in (d, splitting) order, so the list comes out in canonical order.
+    int64_t n = 0;
+    std::vector<std::pair<int, int>> cand;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            for (int c2 = b + 1; c2 < N; ++c2) {
+                cand.clear();
+                const double centre[3] = {omega[b] + omega[c2] - omega[a], omega[a] + omega[b] - omega[c2],
+                                          omega[a] + omega[c2] - omega[b]};
+                for (int t = 0; t < 3; ++t) {
+                    const double *lo = std::lower_bound(omega + c2 + 1, omega + N, centre[t] - gamma);
+                    for (const double *it = lo; it < omega + N && *it <= centre[t] + gamma; ++it) {
+                        const int d = (int)(it - omega);
+                        int p, q, u, v;  // conjugated {p, q}, plain {u, v}
+                        if (t == 0) { p = a; q = d; u = b; v = c2; }
+                        else if (t == 1) { p = a; q = b; u = c2; v = d; }
+                        else { p = a; q = c2; u = b; v = d; }
+                        if (std::fabs(omega[p] + omega[q] - omega[u] - omega[v]) < gamma) cand.push_back({d, t});
+                    }
+                }
+                std::sort(cand.begin(), cand.end());
+                for (const auto &dt : cand) {
+                    const int d = dt.first, t = dt.second;
+                    if (quads) {
+                        int32_t *o = quads + 4 * n;
+                        if (t == 0) { o[0] = a; o[1] = b; o[2] = c2; o[3] = d; }
+                        else if (t == 1) { o[0] = a; o[1] = c2; o[2] = d; o[3] = b; }
+                        else { o[0] = a; o[1] = b; o[2] = d; o[3] = c2; }
+                    }
+                    ++n;
+                }
+            }
+    *count = n;
+    return PT_OK;
+}
+
+static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const int32_t *graph,
+                       const double *J, const int64_t *J_offsets, int n_T, const double *temps, int replicas,
+                       uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);
+
 int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const double *J,
               const int64_t *J_offsets, int n_T, const double *temps, int replicas, uint64_t seed,
               pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream) {
+    return create_impl(out, cfg_in, S, Nv, nullptr, J, J_offsets, n_T, temps, replicas, seed, alloc, free_,
+                       alloc_user, stream);
+}
+
+int pt_create_graph(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const int32_t *quads,
+                    const double *J, const int64_t *q_offsets, int n_T, const double *temps, int replicas,
+                    uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream) {
+    if (!quads) return fail(nullptr, PT_EINVAL, "pt_create_graph: quads is NULL");
+    return create_impl(out, cfg_in, S, Nv, quads, J, q_offsets, n_T, temps, replicas, seed, alloc, free_,
+                       alloc_user, stream);
+}
+
+static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const int32_t *graph,
+                       const double *J, const int64_t *J_offsets, int n_T, const double *temps, int replicas,
+                       uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream) {
     if (!out) return fail(nullptr, PT_EINVAL, "pt_create: out is NULL");
     *out = nullptr;
     pt_config cfg;
@@ -641,11 +705,25 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
         if (t && !(temps[t] > temps[t - 1])) return fail(nullptr, PT_EINVAL, "pt_create: temperatures must be strictly ascending");
     }
     if ((int64_t)S * replicas * n_T > (1ll << 28)) return fail(nullptr, PT_EINVAL, "pt_create: too many chains");
+    if (graph && cfg.precision != PT_PREC_FP64_PLAIN)
+        return fail(nullptr, PT_EUNSUPPORTED, "pt_create_graph: explicit graphs run on the PT_PREC_FP64_PLAIN path");
     for (int s = 0; s < S; ++s) {
         if (Nv[s] < 4 || Nv[s] > 512 || (Nv[s] & 1)) return fail(nullptr, PT_EINVAL, "pt_create: every N must be even, 4..512");
-        int64_t nq;
-        pt_enumerate_quads(Nv[s], nullptr, &nq);
-        if (J_offsets[s + 1] - J_offsets[s] != nq) return fail(nullptr, PT_EINVAL, "pt_create: J_offsets do not match the quadruplet counts");
+        if (graph) {
+            if (J_offsets[s + 1] < J_offsets[s] || (s == 0 && J_offsets[0] != 0))
+                return fail(nullptr, PT_EINVAL, "pt_create_graph: q_offsets must start at 0 and not decrease");
+            for (int64_t q = J_offsets[s]; q < J_offsets[s + 1]; ++q) {
+                const int32_t *Q = graph + 4 * q;
+                for (int m = 0; m < 4; ++m)
+                    if (Q[m] < 0 || Q[m] >= Nv[s]) return fail(nullptr, PT_EINVAL, "pt_create_graph: mode index out of range");
+                if (Q[0] == Q[1] || Q[0] == Q[2] || Q[0] == Q[3] || Q[1] == Q[2] || Q[1] == Q[3] || Q[2] == Q[3])
+                    return fail(nullptr, PT_EINVAL, "pt_create_graph: the four modes of a quadruplet must be distinct");
+            }
+        } else {
+            int64_t nq;
+            pt_enumerate_quads(Nv[s], nullptr, &nq);
+            if (J_offsets[s + 1] - J_offsets[s] != nq) return fail(nullptr, PT_EINVAL, "pt_create: J_offsets do not match the quadruplet counts");
+        }
         for (int64_t i = J_offsets[s]; i < J_offsets[s + 1]; ++i)
             if (!std::isfinite(J[i])) return fail(nullptr, PT_ENAN, "pt_create: non-finite coupling");
     }
@@ -800,8 +878,9 @@ int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, c
             const int n = c->N[s];
             const SampleDev &sd = c->samples[s];
             std::vector<int32_t> abcd((size_t)4 * std::max<int64_t>(sd.nq, 1));
-            int64_t cnt;
-            pt_enumerate_quads(n, abcd.data(), &cnt);
+            int64_t cnt = sd.nq;
+            if (graph) std::copy(graph + 4 * J_offsets[s], graph + 4 * J_offsets[s + 1], abcd.begin());
+            else pt_enumerate_quads(n, abcd.data(), &cnt);
             std::vector<int> deg(n + 1, 0);
             for (int64_t q = 0; q < cnt; ++q) {
                 hq[sd.q_off + q] = make_int4(abcd[4 * q], abcd[4 * q + 1], abcd[4 * q + 2], abcd[4 * q + 3]);

@@ -31,6 +31,12 @@ def couplings(N: int, n_quads: int, seed: int) -> np.ndarray:
     return rng.standard_normal(int(n_quads)) / float(N)
 
 
+def random_frequencies(N: int, seed: int) -> np.ndarray:
+    """Quenched mode frequencies r_k ~ U[0,1], sorted ascending (Sec. II.C "Quenched random frequencies")."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    return np.sort(rng.uniform(0.0, 1.0, size=int(N)))
+
+
 def ragged_sizes(n_samples: int, choices=(32, 48, 64, 96, 128), seed: int = 200) -> np.ndarray:
     """Per-sample mode counts drawn uniformly from `choices` (ragged batch workload)."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))
