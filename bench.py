@@ -289,10 +289,10 @@ def learned_leg():
     return r
 
 
-def graph_leg(sweeps=4):
+def graph_leg(sweeps=64, plain_sweeps=4):
     """The paper's own graph: random mode frequencies with the matching condition of linewidth
-    1/(2(N-1)) (N = 64, 16 samples x 32 T [0.3,1.6] x 2 replicas), on the quadruplet-list FP64 path;
-    a bounded sample of sweeps timed with CUDA events on the library's stream."""
+    1/(2(N-1)) (N = 64, 16 samples x 32 T [0.3,1.6] x 2 replicas): the FP32 group kernels and, on a bounded
+    sample, the FP64 quadruplet-list path; CUDA events on the library's stream."""
     import torch
     import paper_2511_13508_gb300 as pkg
     from paper_2511_13508_gb300 import workload
@@ -300,21 +300,25 @@ def graph_leg(sweeps=4):
     temps = workload.geometric_ladder(0.3, 1.6, 32)
     graphs = [pkg.fmc_graph(workload.random_frequencies(N, 500 + s)) for s in range(S)]
     Js = [workload.couplings(N, len(g), 600 + s) for s, g in enumerate(graphs)]
-    stream = torch.cuda.Stream()
-    pt = pkg.PT([N] * S, Js, temps, R, 31, precision="fp64_plain", stream=stream, graphs=graphs,
-                swap_every=64, measure_every=16, resync_every=64)
-    pt.sweep(1)
-    pt.sync()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    pt.sweep(sweeps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    rate = pt.n_chains * sweeps / (ev0.elapsed_time(ev1) / 1e3)
-    pt.close()
+    out = {}
+    for prec, n in (("fp32", sweeps), ("fp64_plain", plain_sweeps)):
+        stream = torch.cuda.Stream()
+        pt = pkg.PT([N] * S, Js, temps, R, 31, precision=prec, stream=stream, graphs=graphs,
+                    swap_every=64, measure_every=16, resync_every=64)
+        pt.sweep(2)
+        pt.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pt.sweep(n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[prec] = pt.n_chains * n / (ev0.elapsed_time(ev1) / 1e3)
+        pt.close()
     return {"workload": "N=64 random-frequency mode-locked graph (gamma = 1/(2(N-1))), 16 samples x 32 T x 2 "
-                        "replicas, FP64 quadruplet-list path", "value": rate, "unit": "chain-sweeps/s",
-            "quadruplets_per_sample_mean": float(np.mean([len(g) for g in graphs])), "sweeps": sweeps}
+                        "replicas", "value": out["fp32"], "unit": "chain-sweeps/s", "path": "FP32 group kernels",
+            "fp64_plain_value": out["fp64_plain"],
+            "quadruplets_per_sample_mean": float(np.mean([len(g) for g in graphs])),
+            "sweeps": sweeps, "plain_sweeps": plain_sweeps}
 
 
 def profile_case():

@@ -133,9 +133,10 @@ int pt_fmc_graph(int N, const double *omega, double gamma, int32_t *quads, int64
 /* As pt_create, on explicit interaction lists instead of the comb: sample s has the quadruplets
  * quads[4 q_offsets[s] .. 4 q_offsets[s+1]) in term order (term -cc J Re(conj(a_q0) a_q1 a_q2 conj(a_q3)),
  * the four modes distinct and < N[s]) and the couplings J[q_offsets[s] .. q_offsets[s+1]) (q_offsets[0] = 0).
- * Runs on the quadruplet-list path: cfg->precision must be PT_PREC_FP64_PLAIN (PT_EUNSUPPORTED otherwise);
- * pt_fields and pt_autotune are unsupported there, as for that path on the comb.  PT_EINVAL for a bad
- * index or offsets.  The caller keeps ownership of the arrays. */
+ * Runs on the quadruplet-list paths: PT_PREC_FP64_PLAIN (one thread block per chain, FP64) or PT_PREC_FP32
+ * (one thread block per 8 chains of a sample, which read each quadruplet once for all 8; FP32 products,
+ * FP64 energies); PT_EUNSUPPORTED for PT_PREC_FP64.  pt_fields and pt_autotune are unsupported on these
+ * paths.  PT_EINVAL for a bad index or offsets.  The caller keeps ownership of the arrays. */
 int pt_create_graph(pt_ctx **out, const pt_config *cfg, int S, const int32_t *N, const int32_t *quads,
                     const double *J, const int64_t *q_offsets, int n_T, const double *temps, int replicas,
                     uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);

@@ -160,7 +160,7 @@ class PT:
                  measure_every=16, resync_every=64, chains_per_block=0, sweeps_per_unit=0, blocks_per_sm=0,
                  consumer_warps=0, use_graphs=True, watchdog_ms=600000, stream=None, torch_memory=True, graphs=None):
         """graphs: None for the comb graph of every sample; else one [n_s, 4] quadruplet list per sample
-        (term order, e.g. from fmc_graph) with len(J_list[s]) == n_s, on the fp64_plain path."""
+        (term order, e.g. from fmc_graph) with len(J_list[s]) == n_s, on the fp32 or fp64_plain path."""
         L = lib()
         self.Ns = np.ascontiguousarray(Ns, dtype=np.int32)
         self.S, self.R = len(self.Ns), int(replicas)

@@ -166,6 +166,7 @@ struct pt_ctx {
     std::vector<int> N;
     uint64_t seed = 0;
     bool dbl = false, plain = false;
+    bool gfp32 = false;  // explicit interaction lists on the FP32 group kernels
     cudaStream_t stream = nullptr;
     pt_alloc_fn alloc = nullptr;
     pt_free_fn free_ = nullptr;
@@ -196,6 +197,8 @@ struct pt_ctx {
     double *d_snap_E = nullptr;
     int n_snap_max = 0, max_seg = 0;
     int4 *d_quads = nullptr;
+    int4 *d_rec = nullptr;     // incidence records of the FP32 quadruplet-list path
+    float *d_recJ = nullptr;
     double *d_Jq = nullptr;
     int *d_inc_off = nullptr, *d_inc = nullptr;
     int G = 8, ncw = 8, spu = 1, grid = 1;
@@ -272,7 +275,24 @@ int watchdog_sync(pt_ctx *c) {
 }
 
 // ---------------------------------------------------------------------------------- kernels
+GraphParams graph_params(pt_ctx *c) {
+    GraphParams p{};
+    p.samples = c->d_samples; p.groups = c->d_groups; p.quads = c->d_quads; p.Jd = c->d_Jq;
+    p.inc_off = c->d_inc_off; p.rec = c->d_rec; p.recJ = c->d_recJ; p.a = reinterpret_cast<float2 *>(c->d_a);
+    p.E = c->d_E; p.label = c->d_label; p.beta = c->d_beta; p.mc_acc = c->d_mc_acc; p.mc_att = c->d_mc_att;
+    p.R = c->R; p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
+    p.measure_every = c->cfg.measure_every; p.snap_a = reinterpret_cast<float2 *>(c->d_snap_a);
+    p.snap_E = c->d_snap_E; p.n_snap_max = c->n_snap_max; p.a_total = c->a_total; p.n_chains = c->n_chains;
+    return p;
+}
+
 int run_energy(pt_ctx *c, int renorm, double *E_out, bool write_state) {
+    if (c->gfp32) {
+        GraphParams p = graph_params(c);
+        p.renorm = renorm; p.E_out = E_out; p.E_state = write_state ? c->d_E : nullptr;
+        CK(launch_graph_energy(p, (int)c->groups.size(), c->stream));
+        return PT_OK;
+    }
     if (c->plain) {
         PlainParams p{};
         p.samples = c->d_samples; p.chain_sample = c->d_chain_sample; p.quads = c->d_quads; p.Jq = c->d_Jq;
@@ -312,6 +332,12 @@ int run_swap(pt_ctx *c) {
 }
 
 int run_sweeps(pt_ctx *c, int seg) {
+    if (c->gfp32) {
+        GraphParams p = graph_params(c);
+        p.n_sweeps = seg;
+        CK(launch_graph_sweep(p, (int)c->groups.size(), c->stream));
+        return PT_OK;
+    }
     if (c->plain) {
         PlainParams p{};
         p.samples = c->d_samples; p.chain_sample = c->d_chain_sample; p.quads = c->d_quads; p.Jq = c->d_Jq;
@@ -705,8 +731,8 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         if (t && !(temps[t] > temps[t - 1])) return fail(nullptr, PT_EINVAL, "pt_create: temperatures must be strictly ascending");
     }
     if ((int64_t)S * replicas * n_T > (1ll << 28)) return fail(nullptr, PT_EINVAL, "pt_create: too many chains");
-    if (graph && cfg.precision != PT_PREC_FP64_PLAIN)
-        return fail(nullptr, PT_EUNSUPPORTED, "pt_create_graph: explicit graphs run on the PT_PREC_FP64_PLAIN path");
+    if (graph && cfg.precision == PT_PREC_FP64)
+        return fail(nullptr, PT_EUNSUPPORTED, "pt_create_graph: explicit graphs run in PT_PREC_FP32 or PT_PREC_FP64_PLAIN");
     for (int s = 0; s < S; ++s) {
         if (Nv[s] < 4 || Nv[s] > 512 || (Nv[s] & 1)) return fail(nullptr, PT_EINVAL, "pt_create: every N must be even, 4..512");
         if (graph) {
@@ -734,6 +760,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     c->maxN = *std::max_element(c->N.begin(), c->N.end());
     c->dbl = cfg.precision != PT_PREC_FP32;
     c->plain = cfg.precision == PT_PREC_FP64_PLAIN;
+    c->gfp32 = graph != nullptr && cfg.precision == PT_PREC_FP32;
     c->esize = c->dbl ? 8 : 4;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->alloc = alloc; c->free_ = free_; c->user = alloc_user;
@@ -770,6 +797,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
     // N >= 128: 8 chains x 11 warps; 48 <= N < 128: 32 x 7 when a sample has >= 32 chains; else 16 x 7
     int G = cfg.chains_per_block, ncw = 0;
+    if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
     if (G == 0) {
         if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
         else if (c->maxN >= 128) G = 8;
@@ -780,7 +808,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     if (c->dbl) ncw = (G == 16) ? 3 : 7;
     else ncw = (G == 8) ? (c->maxN >= 128 ? 11 : 7) : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
-    if (!c->plain && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
+    if (!c->plain && !c->gfp32 && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;
     c->spu = cfg.sweeps_per_unit > 0 ? cfg.sweeps_per_unit
                                      : (c->maxN >= 192 ? 1 : c->maxN >= 96 ? 2 : c->maxN >= 48 ? 8 : 32);
@@ -859,7 +887,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     RC(dalloc(c, &c->d_ctl, 1));
 
     // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
-    if (!c->plain) {
+    if (!c->plain && !c->gfp32) {
         const size_t js = c->dbl ? JStride<double>::value : JStride<float>::value;
         c->d_J = dev_alloc(c, (size_t)jblocks * js * c->esize);
         if (!c->d_J) return bail(fail(c, PT_ENOMEM, "device allocation failed (couplings)"));
@@ -870,7 +898,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         }
         CK(cudaMemcpy(c->d_J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
     }
-    if (c->plain || c->maxN <= 64) {
+    if (c->plain || c->gfp32 || c->maxN <= 64) {
         std::vector<int4> hq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<double> hJq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<int> hinc_off, hinc((size_t)std::max<int64_t>(inc_total, 1));
@@ -904,6 +932,33 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         CK(cudaMemcpy(c->d_Jq, hJq.data(), hJq.size() * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->d_inc_off, hinc_off.data(), hinc_off.size() * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->d_inc, hinc.data(), hinc.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (c->gfp32) {
+            // incidence records: for each mode l and quadruplet q holding it, the other three modes in
+            // position order and (q << 2) | position of l, with J_q alongside
+            std::vector<int4> hrec(hinc.size());
+            std::vector<float> hrecJ(hinc.size());
+            for (int s = 0; s < S; ++s) {
+                const SampleDev &sd = c->samples[s];
+                const int *off = hinc_off.data() + sd.mode_off;
+                for (int l = 0; l < c->N[s]; ++l)
+                    for (int e = off[l]; e < off[l + 1]; ++e) {
+                        const int q = hinc[sd.inc_off + e];
+                        const int4 Q = hq[sd.q_off + q];
+                        const int m4[4] = {Q.x, Q.y, Q.z, Q.w};
+                        int pos = 0, o[3] = {0, 0, 0}, n = 0;
+                        for (int m = 0; m < 4; ++m) {
+                            if (m4[m] == l) pos = m;
+                            else if (n < 3) o[n++] = m4[m];
+                        }
+                        hrec[sd.inc_off + e] = make_int4(o[0], o[1], o[2], (q << 2) | pos);
+                        hrecJ[sd.inc_off + e] = (float)hJq[sd.q_off + q];
+                    }
+            }
+            RC(dalloc(c, &c->d_rec, hrec.size()));
+            RC(dalloc(c, &c->d_recJ, hrecJ.size()));
+            CK(cudaMemcpy(c->d_rec, hrec.data(), hrec.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->d_recJ, hrecJ.data(), hrecJ.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
     }
     std::vector<int> label(c->n_chains), perm(c->n_chains);
     for (int s = 0; s < S; ++s)
@@ -940,7 +995,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     CK(cudaMemset(c->d_ctl, 0, sizeof(Control)));
 
     // ---- persistent grid
-    if (!c->plain) {
+    if (!c->plain && !c->gfp32) {
         int dev = 0, sms = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1150,7 +1205,7 @@ int pt_energy(pt_ctx *c, double *E) {
 
 int pt_fields(pt_ctx *c, int sample, int j, int k, double *out) {
     if (!c || !out) return fail(c, PT_EINVAL, "pt_fields: NULL argument");
-    if (c->plain) return fail(c, PT_EUNSUPPORTED, "pt_fields: not available for the plain FP64 path");
+    if (c->plain || c->gfp32) return fail(c, PT_EUNSUPPORTED, "pt_fields: not available for the quadruplet-list paths");
     if (sample < 0 || sample >= c->S) return fail(c, PT_EINVAL, "pt_fields: bad sample");
     const int N = c->N[sample];
     if (j < 0 || j >= N || k < 0 || k >= N || j == k) return fail(c, PT_EINVAL, "pt_fields: need distinct modes in [0, N)");
@@ -1282,7 +1337,7 @@ int pt_load(pt_ctx *c, const void *buf, size_t len) {
 
 int pt_autotune(pt_ctx *c, int trial_sweeps, int *chosen) {
     if (!c) return fail(nullptr, PT_EINVAL, "pt_autotune: NULL context");
-    if (c->plain) return fail(c, PT_EUNSUPPORTED, "pt_autotune: the plain FP64 path has one shape");
+    if (c->plain || c->gfp32) return fail(c, PT_EUNSUPPORTED, "pt_autotune: the quadruplet-list paths have one shape");
     if (trial_sweeps < 1) return fail(c, PT_EINVAL, "pt_autotune: trial_sweeps must be >= 1");
     size_t len = 0;
     int rc = pt_save(c, nullptr, &len);

@@ -118,6 +118,36 @@ struct MeasureParams {
 cudaError_t launch_measure(const MeasureParams &p, cudaStream_t s);
 
 // Plain FP64 path: the paper's design restated (one block per chain, one thread per quadruplet term).
+// pt_graph.cu: FP32 sweep / energy on explicit interaction lists (one block per group of 8 chains)
+struct GraphParams {
+    const SampleDev *samples;
+    const GroupDev *groups;
+    const int4 *quads;       // quadruplets in term order, per sample at q_off (energy kernel)
+    const double *Jd;        // FP64 couplings (energy kernel)
+    const int *inc_off;      // per sample mode: offsets into the incidence records (N+1, at mode_off)
+    const int4 *rec;         // incidence records per mode (at inc_off): other three modes, (q << 2) | position
+    const float *recJ;       // coupling of each incidence record
+    float2 *a;
+    double *E;
+    const int *label;
+    const double *beta;
+    unsigned long long *mc_acc, *mc_att;
+    int R, nT, maxN;
+    uint64_t seed;
+    double cc;
+    Control *ctl;
+    int n_sweeps, measure_every;
+    float2 *snap_a;
+    double *snap_E;
+    int n_snap_max;
+    int64_t a_total;
+    int n_chains;
+    int renorm;              // energy kernel: rescale to sum |a|^4 = N first
+    double *E_out, *E_state; // energy kernel outputs (optional)
+};
+cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s);
+cudaError_t launch_graph_energy(const GraphParams &p, int n_groups, cudaStream_t s);
+
 struct PlainParams {
     const SampleDev *samples;
     const int *chain_sample;
