@@ -321,6 +321,39 @@ def graph_leg(sweeps=64, plain_sweeps=4):
             "sweeps": sweeps, "plain_sweeps": plain_sweeps}
 
 
+def ladder_leg():
+    """App. A: specific heat on a ladder of fixed Delta T (N = 64 comb, 8 samples x 32 T [0.2,1.6] x 2
+    replicas), the ladder T_i = T_{i-1}/(1 - 0.6/sqrt(C_V(T_i))), and the swap acceptance per neighbouring
+    pair on it and on a geometric ladder of the same size and end points."""
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import analysis, workload
+    N, S, R = 64, 8, 2
+    Js = [workload.couplings(N, len(pkg.enumerate_quads(N)), 800 + s) for s in range(S)]
+
+    def rates(temps, sweeps=8192, burn=2048):
+        pt = pkg.PT([N] * S, Js, temps, R, 5, precision="fp32", swap_every=16, measure_every=4, resync_every=64)
+        pt.sweep(burn)
+        pt.reset_observables()
+        pt.sweep(sweeps)
+        o = pt.observables()
+        acc = o["swap_acc"].sum((0, 1)) / np.maximum(o["swap_att"].sum((0, 1)), 1)
+        cv, _ = analysis.specific_heat(o, temps)
+        pt.close()
+        return acc, cv
+
+    Tlin = np.linspace(0.2, 1.6, 32)
+    _, cv = rates(Tlin)
+    Tad = analysis.adaptive_ladder(Tlin, cv, 0.2, 1.6, 0.6)
+    Tgeo = workload.geometric_ladder(0.2, 1.6, len(Tad))
+    a_ad, _ = rates(Tad)
+    a_geo, _ = rates(Tgeo)
+    inner = slice(0, len(Tad) - 2)
+    stat = lambda a: {"mean": float(a[inner].mean()), "min": float(a[inner].min()),
+                      "rel_spread": float(a[inner].std() / a[inner].mean())}
+    return {"workload": "N=64 comb, 8 samples x 2 replicas, C = 0.6, T in [0.2, 1.6]", "n_temps": len(Tad),
+            "temps": [round(float(t), 4) for t in Tad], "adaptive": stat(a_ad), "geometric": stat(a_geo)}
+
+
 def profile_case():
     """Three launches of the sweep kernel (one sweep each) on half the bench workload: 8 samples
     (176 MB of couplings, larger than L2), 768 chains; no measurement, resync or swap."""
@@ -349,6 +382,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal ESS comparison")
     ap.add_argument("--no-graph", action="store_true", help="skip the random-frequency graph leg")
+    ap.add_argument("--no-ladder", action="store_true", help="skip the adaptive-ladder leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     args = ap.parse_args()
@@ -396,6 +430,9 @@ def main():
     graph = None
     if rank == 0 and world == 1 and not args.no_graph:
         graph = graph_leg()
+    ladder = None
+    if rank == 0 and world == 1 and not args.no_ladder:
+        ladder = ladder_leg()
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -413,7 +450,8 @@ def main():
                 "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
                                    "speedup_fp32": r["value"] / world / r["plain_rate"]},
                 "learned_vs_plain": learned,
-                "random_graph": graph}
+                "random_graph": graph,
+                "adaptive_ladder": ladder}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

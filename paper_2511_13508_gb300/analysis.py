@@ -111,3 +111,43 @@ def thermalised(windows, temps, key: str = "E", z: float = 3.0) -> np.ndarray:
     b = thermal_averages(windows[-1], temps)[key]
     d, err = jackknife(b - a)
     return np.abs(d) <= z * err + 1e-12
+
+
+def adaptive_ladder(T_grid, CV_grid, T_min: float, T_max: float, C: float = 0.6, tol: float = 1e-12,
+                    max_temps: int = 4096) -> np.ndarray:
+    """Temperatures of App. A, Eq. (PT_Ti): T_0 = T_min and T_i = T_{i-1} / (1 - C / sqrt(C_V(T_i))) while
+    T_i < T_max, then T_max; so that Delta T ~ T / sqrt(C_V(T)) and neighbouring swaps are accepted at a
+    similar rate.  C_V(T) is the measured specific heat (per sample, disorder-averaged) interpolated
+    linearly on (T_grid, CV_grid) and held constant outside it.  The recursion is implicit (C_V at the
+    new temperature) and is solved by fixed-point iteration from C_V(T_{i-1}).
+    ValueError where C >= sqrt(C_V) (no finite step)."""
+    Tg = np.asarray(T_grid, np.float64)
+    Cg = np.asarray(CV_grid, np.float64)
+    order = np.argsort(Tg)
+    Tg, Cg = Tg[order], Cg[order]
+
+    def cv(T):
+        return float(np.interp(T, Tg, Cg))
+
+    def step(Tp, Cv):
+        d = 1.0 - C / np.sqrt(Cv)
+        if not (Cv > 0.0) or d <= 0.0:
+            raise ValueError("adaptive_ladder: C >= sqrt(C_V) near T = %g (C_V = %g)" % (Tp, Cv))
+        return Tp / d
+
+    out = [float(T_min)]
+    while len(out) < max_temps:
+        Tp = out[-1]
+        T = step(Tp, cv(Tp))
+        for _ in range(200):
+            Tn = step(Tp, cv(T))
+            if abs(Tn - T) <= tol * max(1.0, abs(T)):
+                T = Tn
+                break
+            T = Tn
+        if T >= T_max:
+            break
+        out.append(T)
+    if out[-1] < T_max:
+        out.append(float(T_max))
+    return np.asarray(out)

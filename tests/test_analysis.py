@@ -97,3 +97,32 @@ def test_doubling_windows_detect_relaxation_on_oracle_runs():
     assert np.all(analysis.thermalised(w, temps))
     E = [analysis.disorder_average(analysis.thermal_averages(x, temps)["E"])[0][0] for x in w]
     assert E[-1] < E[0]
+
+
+def test_adaptive_ladder_is_geometric_for_constant_specific_heat():
+    """C_V = c: T_i = T_{i-1} / (1 - C/sqrt(c)) exactly, up to T_max."""
+    c, C = 9.0, 0.6
+    T = analysis.adaptive_ladder([0.1, 2.0], [c, c], 0.2, 1.0, C)
+    r = 1.0 / (1.0 - C / 3.0)
+    expect = 0.2 * r ** np.arange(len(T) - 1)
+    assert np.allclose(T[:-1], expect, rtol=1e-13) and T[-1] == 1.0 and expect[-1] * r >= 1.0
+
+
+def test_adaptive_ladder_solves_the_implicit_recursion():
+    """C_V(T) = a / T^2 (the high-temperature form beta^2 Var_0(H)): the implicit step
+    T_i (1 - C T_i / sqrt(a)) = T_{i-1} has the closed-form root T_i = (1 - sqrt(1 - 4 b T_{i-1})) / (2 b),
+    b = C / sqrt(a)."""
+    a, C = 400.0, 0.6
+    Tg = np.linspace(0.05, 3.0, 20001)
+    T = analysis.adaptive_ladder(Tg, a / Tg ** 2, 0.2, 1.0, C)
+    b = C / math.sqrt(a)
+    prev = 0.2
+    for t in T[1:-1]:
+        root = (1 - math.sqrt(1 - 4 * b * prev)) / (2 * b)
+        assert abs(t - root) < 1e-6 * root
+        prev = t
+
+
+def test_adaptive_ladder_rejects_too_small_specific_heat():
+    with pytest.raises(ValueError):
+        analysis.adaptive_ladder([0.1, 2.0], [0.25, 0.25], 0.2, 1.0, 0.6)

@@ -43,3 +43,36 @@ def test_kurtosis_and_specific_heat_match_the_oracle():
     chi_g = analysis.pq_symmetry(og["qhist"])
     chi_o = analysis.pq_symmetry(oo["qhist"])
     assert np.nanmedian(chi_g) < 4.0 and np.nanmedian(chi_o) < 4.0, (np.nanmedian(chi_g), np.nanmedian(chi_o))
+
+
+def _swap_rates(N, S, R, Js, temps, sweeps=8192, burn=2048):
+    pt = pkg.PT([N] * S, Js, temps, R, 5, precision="fp32", swap_every=16, measure_every=4, resync_every=64)
+    pt.sweep(burn)
+    pt.reset_observables()
+    pt.sweep(sweeps)
+    o = pt.observables()
+    acc = o["swap_acc"].sum((0, 1)) / np.maximum(o["swap_att"].sum((0, 1)), 1)
+    cv, _ = analysis.specific_heat(o, temps)
+    pt.close()
+    return acc, cv
+
+
+def test_adaptive_ladder_equalises_swap_acceptance():
+    """App. A: C_V(T) measured on a ladder of fixed Delta T gives, through T_i = T_{i-1}/(1 - C/sqrt(C_V)),
+    a ladder whose neighbouring swaps are accepted at a nearly uniform rate, unlike a geometric ladder of
+    the same size and end points."""
+    N, S, R = 64, 8, 2
+    Js = [workload.couplings(N, len(pkg.enumerate_quads(N)), 800 + s) for s in range(S)]
+    Tlin = np.linspace(0.2, 1.6, 32)
+    _, cv = _swap_rates(N, S, R, Js, Tlin)
+    Tad = analysis.adaptive_ladder(Tlin, cv, 0.2, 1.6, 0.6)
+    Tgeo = workload.geometric_ladder(0.2, 1.6, len(Tad))
+    a_ad, _ = _swap_rates(N, S, R, Js, Tad)
+    a_geo, _ = _swap_rates(N, S, R, Js, Tgeo)
+    inner = slice(0, len(Tad) - 2)  # the last step is cut at T_max
+    spread_ad = a_ad[inner].std() / a_ad[inner].mean()
+    spread_geo = a_geo[inner].std() / a_geo[inner].mean()
+    print(f"adaptive ladder ({len(Tad)} T): swap acceptance mean {a_ad[inner].mean():.3f} spread {spread_ad:.3f}; "
+          f"geometric: mean {a_geo[inner].mean():.3f} spread {spread_geo:.3f}")
+    assert spread_ad < 0.5 * spread_geo
+    assert a_ad[inner].min() > a_geo[inner].min()
