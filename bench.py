@@ -314,11 +314,30 @@ def graph_leg(sweeps=64, plain_sweeps=4):
         torch.cuda.synchronize()
         out[prec] = pt.n_chains * n / (ev0.elapsed_time(ev1) / 1e3)
         pt.close()
+    # a sparse mode-locked graph far beyond the comb's size: N = 2048, 16 quadruplets per mode
+    Ns2 = 2048
+    sg = [workload.sparse_comb_graph(Ns2, 16, 700 + s) for s in range(S)]
+    sJ = [workload.couplings(Ns2, len(g), 800 + s) * Ns2 for s, g in enumerate(sg)]
+    stream = torch.cuda.Stream()
+    pt = pkg.PT([Ns2] * S, sJ, temps, R, 37, precision="fp32", stream=stream, graphs=sg,
+                swap_every=64, measure_every=16, resync_every=64)
+    pt.sweep(1)
+    pt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pt.sweep(4)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sparse = pt.n_chains * 4 / (ev0.elapsed_time(ev1) / 1e3)
+    pt.close()
     return {"workload": "N=64 random-frequency mode-locked graph (gamma = 1/(2(N-1))), 16 samples x 32 T x 2 "
                         "replicas", "value": out["fp32"], "unit": "chain-sweeps/s", "path": "FP32 group kernels",
             "fp64_plain_value": out["fp64_plain"],
             "quadruplets_per_sample_mean": float(np.mean([len(g) for g in graphs])),
-            "sweeps": sweeps, "plain_sweeps": plain_sweeps}
+            "sweeps": sweeps, "plain_sweeps": plain_sweeps,
+            "sparse_n2048_z16": {"value": sparse, "unit": "chain-sweeps/s", "sweeps": 4,
+                                 "workload": "N=2048 sparse comb graph, 16 quadruplets per mode, 16 samples x 32 T "
+                                             "x 2 replicas, FP32 group kernels"}}
 
 
 def ladder_leg():

@@ -132,7 +132,8 @@ int pt_fmc_graph(int N, const double *omega, double gamma, int32_t *quads, int64
 
 /* As pt_create, on explicit interaction lists instead of the comb: sample s has the quadruplets
  * quads[4 q_offsets[s] .. 4 q_offsets[s+1]) in term order (term -cc J Re(conj(a_q0) a_q1 a_q2 conj(a_q3)),
- * the four modes distinct and < N[s]) and the couplings J[q_offsets[s] .. q_offsets[s+1]) (q_offsets[0] = 0).
+ * the four modes distinct and < N[s]) and the couplings J[q_offsets[s] .. q_offsets[s+1]) (q_offsets[0] = 0);
+ * every N[s] even, 4..2048.
  * Runs on the quadruplet-list paths: PT_PREC_FP64_PLAIN (one thread block per chain, FP64) or PT_PREC_FP32
  * (one thread block per 8 chains of a sample, which read each quadruplet once for all 8; FP32 products,
  * FP64 energies); PT_EUNSUPPORTED for PT_PREC_FP64.  pt_fields and pt_autotune are unsupported on these

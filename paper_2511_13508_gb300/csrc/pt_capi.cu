@@ -734,7 +734,9 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     if (graph && cfg.precision == PT_PREC_FP64)
         return fail(nullptr, PT_EUNSUPPORTED, "pt_create_graph: explicit graphs run in PT_PREC_FP32 or PT_PREC_FP64_PLAIN");
     for (int s = 0; s < S; ++s) {
-        if (Nv[s] < 4 || Nv[s] > 512 || (Nv[s] & 1)) return fail(nullptr, PT_EINVAL, "pt_create: every N must be even, 4..512");
+        if (Nv[s] < 4 || Nv[s] > (graph ? 2048 : 512) || (Nv[s] & 1))
+            return fail(nullptr, PT_EINVAL, graph ? "pt_create_graph: every N must be even, 4..2048"
+                                                  : "pt_create: every N must be even, 4..512");
         if (graph) {
             if (J_offsets[s + 1] < J_offsets[s] || (s == 0 && J_offsets[0] != 0))
                 return fail(nullptr, PT_EINVAL, "pt_create_graph: q_offsets must start at 0 and not decrease");
@@ -844,7 +846,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     c->n_chains = chain0;
     c->a_total = a_off;
     make_groups(c, G);
-    c->max_groups = (size_t)S * ((chains_ps + 7) / 8);
+    c->max_groups = std::max((size_t)S * ((chains_ps + 7) / 8), c->groups.size());
     // ---- schedule buffers
     int ev = 0;
     for (int e : {cfg.swap_every, cfg.resync_every}) if (e > 0) ev = ev ? std::min(ev, e) : e;
@@ -994,6 +996,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     CK(cudaMemset(c->d_qstat, 0, (size_t)S * n_T * PT_NQSTAT * sizeof(double)));
     CK(cudaMemset(c->d_ctl, 0, sizeof(Control)));
 
+    if (c->gfp32) CK(graph_prepare(c->maxN));
     // ---- persistent grid
     if (!c->plain && !c->gfp32) {
         int dev = 0, sms = 0;

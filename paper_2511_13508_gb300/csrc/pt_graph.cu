@@ -269,6 +269,13 @@ __global__ void __launch_bounds__(kGThreads) graph_energy_kernel(GraphParams p) 
     }
 }
 
+cudaError_t graph_prepare(int maxN) {
+    const int sm = maxN * kGRS * (int)sizeof(float2);  // 72 B per mode: 147 KB at N = 2048
+    cudaError_t e = cudaFuncSetAttribute(graph_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s) {
     if (n_groups <= 0) return cudaSuccess;
     const size_t sm = (size_t)p.maxN * kGRS * sizeof(float2);

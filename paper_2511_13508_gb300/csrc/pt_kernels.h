@@ -147,6 +147,7 @@ struct GraphParams {
 };
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s);
 cudaError_t launch_graph_energy(const GraphParams &p, int n_groups, cudaStream_t s);
+cudaError_t graph_prepare(int maxN);  // shared-memory limit of the graph kernels for N up to maxN
 
 struct PlainParams {
     const SampleDev *samples;

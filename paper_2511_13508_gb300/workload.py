@@ -37,6 +37,24 @@ def random_frequencies(N: int, seed: int) -> np.ndarray:
     return np.sort(rng.uniform(0.0, 1.0, size=int(N)))
 
 
+def sparse_comb_graph(N: int, z: float, seed: int) -> np.ndarray:
+    """A sparse mode-locked graph (the finite-connectivity networks of Sec. II.D and Sec. V): round(z N / 4)
+    quadruplets of the comb (a<b<c<d with a+d = b+c, term order (a, b, c, d)) drawn uniformly without
+    replacement, so every mode holds z of them on average.  A uniform (a, b, c) with d = b + c - a is kept
+    when c < d < N, which makes every comb quadruplet equally likely."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    M = int(round(z * N / 4))
+    seen, out = set(), []
+    while len(out) < M:
+        a, b, c = np.sort(rng.choice(N, 3, replace=False))
+        d = b + c - a
+        if c < d < N and (a, b, c) not in seen:
+            seen.add((a, b, c))
+            out.append((a, b, c, d))
+    out.sort()
+    return np.asarray(out, dtype=np.int32).reshape(-1, 4)
+
+
 def ragged_sizes(n_samples: int, choices=(32, 48, 64, 96, 128), seed: int = 200) -> np.ndarray:
     """Per-sample mode counts drawn uniformly from `choices` (ragged batch workload)."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))

@@ -123,3 +123,30 @@ def test_fp32_graph_long_run_matches_oracle_statistically():
     a, E = gpu.state()
     assert np.allclose(gpu.energy(), E, rtol=1e-4, atol=1e-4)
     assert np.allclose([(np.abs(x) ** 4).sum() for x in _split(a, Ns, R, nT)], 16, rtol=1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64_plain", "fp32"])
+def test_sparse_graphs_beyond_the_comb_size_limit(prec):
+    """Sparse mode-locked graphs (z quadruplets per mode, unit couplings' scale) at N = 512 .. 2048: the FP64
+    path follows the oracle's chain; the FP32 path keeps the constraint and its running energies equal to
+    the oracle's energies of its states."""
+    Ns, R, nT = [512, 2048], 2, 2
+    graphs = [workload.sparse_comb_graph(n, 16, 40 + n) for n in Ns]
+    Js = [workload.couplings(n, len(g), 70 + n) * n for n, g in zip(Ns, graphs)]  # sigma_J = 1 (c ~ N)
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    kw = dict(swap_every=2, measure_every=1, resync_every=4)
+    pt = pkg.PT(Ns, Js, temps, R, 19, precision=prec, graphs=graphs, **kw)
+    pt.sweep(6)
+    a1, E1 = pt.state()
+    if prec == "fp64_plain":
+        ref = oracle.OraclePT(Ns, Js, temps, R, 19, graphs=graphs, **kw)
+        ref.sweep(6)
+        a0, E0 = ref.state()
+        assert np.abs(a1 - a0).max() < 1e-9
+        assert np.allclose(E1, E0, rtol=1e-9, atol=1e-9)
+    else:
+        per = [(n, g, J) for n, g, J in zip(Ns, graphs, Js) for _ in range(R * nT)]
+        xs = _split(a1, Ns, R, nT)
+        Eo = [oracle.energy(n, g, J, x) for (n, g, J), x in zip(per, xs)]
+        assert np.allclose(E1, Eo, rtol=1e-4, atol=1e-3)
+        assert np.allclose([(np.abs(x) ** 4).sum() / len(x) for x in xs], 1.0, rtol=1e-4)

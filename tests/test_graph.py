@@ -94,3 +94,17 @@ def test_oracle_pt_on_random_graphs():
             assert abs((np.abs(x) ** 4).sum() - n) < 1e-10 * n
             assert abs(oracle.energy(n, graphs[s], Js[s], x) - E[s * 8 + c]) < 1e-9
             off += n
+
+
+@pytest.mark.parametrize("N,z", [(64, 4), (512, 8), (2048, 16)])
+def test_sparse_comb_graph(N, z):
+    """Finite connectivity: round(z N / 4) distinct comb quadruplets, z per mode on average."""
+    g = workload.sparse_comb_graph(N, z, 3)
+    assert len(g) == round(z * N / 4)
+    assert np.all(g[:, 0] + g[:, 3] == g[:, 1] + g[:, 2])
+    assert np.all((g[:, 0] < g[:, 1]) & (g[:, 1] < g[:, 2]) & (g[:, 2] < g[:, 3])) and g.min() >= 0 and g.max() < N
+    assert len({tuple(q) for q in g.tolist()}) == len(g)
+    assert abs(np.bincount(g.ravel(), minlength=N).mean() - z) < 1e-12
+    if N == 64:  # every listed quadruplet belongs to the comb list
+        comb = {tuple(q) for q in oracle.enumerate_quads(N).tolist()}
+        assert all(tuple(q) in comb for q in g.tolist())
