@@ -251,6 +251,13 @@ int pt_learn_shape(pt_ctx *ctx, int64_t *out);
 int pt_learn_eval(pt_ctx *ctx, const double *a, const int *cond, int rows, double *logq, double *extra,
                   float *grad);
 
+/* Health check of the failure detection: launches a one-thread kernel that waits, bounded by limit_ms
+ * (1..60000), on a device flag that no kernel sets, so the wait always runs out and records the timeout
+ * status the engine's own bounded waits record.  Returns what the synchronising calls then report,
+ * PT_ETIMEOUT, and clears the status afterwards, so the context stays usable with its state untouched.
+ * PT_EINVAL for a bad limit; another code if the context already carried an error. */
+int pt_check_wait(pt_ctx *ctx, int limit_ms);
+
 /* Counters: sweeps done since creation, swap passes done. */
 int pt_counters(pt_ctx *ctx, int64_t *sweeps_done, int64_t *swap_passes);
 

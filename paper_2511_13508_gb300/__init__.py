@@ -50,7 +50,7 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
            "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_gemm_bf16",
-           "pt_energy_fp64_static", "pt_fmc_graph", "pt_create_graph"]
+           "pt_energy_fp64_static", "pt_fmc_graph", "pt_create_graph", "pt_check_wait"]
 
 _lib = None
 
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.pt_create_graph.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), i, vp, vp, vp, vp, i, vp, i, u64,
                                       ALLOC_FN, FREE_FN, vp, vp]
         L.pt_fmc_graph.argtypes = [i, vp, d, vp, ctypes.POINTER(i64)]
+        L.pt_check_wait.argtypes = [vp, i]
         L.pt_sweep.argtypes = [vp, i64]
         for n in ("pt_swap", "pt_resync", "pt_measure_now", "pt_reset_observables", "pt_sync", "pt_destroy"):
             getattr(L, n).argtypes = [vp]
@@ -290,6 +291,11 @@ class PT:
         return tuple(out)
 
     # ------------------------------------------------------------------ learned global-move proposal
+    def check_wait(self, limit_ms=200) -> int:
+        """Runs the bounded-wait health check (pt_check_wait); returns its status code (PT_ETIMEOUT = -4
+        when the failure detection works) without raising."""
+        return int(lib().pt_check_wait(self._h, int(limit_ms)))
+
     def learn_init(self, n_cold=8, batch=512, data_per_sample=1 << 14, seed=0):
         self._c(lib().pt_learn_init(self._h, int(n_cold), int(batch), int(data_per_sample), ctypes.c_uint64(int(seed))))
 

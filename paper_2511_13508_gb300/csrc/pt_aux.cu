@@ -329,6 +329,25 @@ cudaError_t launch_plain_energy(const PlainParams &p, int n_chains, cudaStream_t
     return cudaGetLastError();
 }
 
+// Health check of the bounded waits: waits on a flag no kernel sets until the limit, then records the
+// same timeout status as the engine's own waits.
+__global__ void wait_probe_kernel(Control *ctl, unsigned long long limit_ns) {
+    const volatile int *flag = &ctl->probe_flag;
+    const unsigned long long t0 = global_ns();
+    while (*flag == 0) {
+        if (global_ns() - t0 > limit_ns) {
+            record_error(ctl, kErrTimeout, 40);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+cudaError_t launch_wait_probe(Control *ctl, unsigned long long limit_ns, cudaStream_t s) {
+    wait_probe_kernel<<<1, 1, 0, s>>>(ctl, limit_ns);
+    return cudaGetLastError();
+}
+
 __global__ void advance_kernel(Control *ctl, long long sweeps, long long passes, long long rounds) {
     ctl->sweep_base += sweeps;
     ctl->swap_passes += passes;

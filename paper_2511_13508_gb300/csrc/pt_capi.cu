@@ -1649,6 +1649,19 @@ int pt_set_global_blocks(pt_ctx *c, int lo, int hi) {
     return PT_OK;
 }
 
+int pt_check_wait(pt_ctx *c, int limit_ms) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_check_wait: NULL context");
+    if (limit_ms < 1 || limit_ms > 60000) return fail(c, PT_EINVAL, "pt_check_wait: limit_ms must be 1..60000");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    CK(launch_wait_probe(c->d_ctl, (unsigned long long)limit_ms * 1000000ull, c->stream));
+    rc = watchdog_sync(c);
+    // clear the status the probe left, so that the context goes on
+    const int zero[2] = {0, 0};
+    CK(cudaMemcpy(&c->d_ctl->error, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return rc;
+}
+
 int pt_counters(pt_ctx *c, int64_t *sweeps_done, int64_t *swap_passes) {
     if (!c) return fail(nullptr, PT_EINVAL, "pt_counters: NULL context");
     if (sweeps_done) *sweeps_done = c->sweeps_done;

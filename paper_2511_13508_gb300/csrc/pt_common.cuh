@@ -101,7 +101,7 @@ struct GroupDev {
     int sample;
     int chain0;  // first chain slot
     int count;   // chains in the group (<= G)
-    int pad_;
+    int probe_flag;         // written by no kernel: the wait probe waits on it until its limit
 };
 
 // Kernel-wide control words in device memory.
@@ -109,7 +109,7 @@ struct Control {
     unsigned int ticket;    // persistent work queue ticket
     int error;              // first error code seen by a kernel (0 = none)
     int error_where;        // where a bounded wait ran out
-    int pad_;
+    int probe_flag;         // written by no kernel: the wait probe waits on it until its limit
     long long sweep_base;   // sweeps done before the current sweep launch
     long long swap_passes;  // swap passes done
     long long global_rounds;  // learned global-move rounds done

@@ -145,6 +145,7 @@ struct GraphParams {
     int renorm;              // energy kernel: rescale to sum |a|^4 = N first
     double *E_out, *E_state; // energy kernel outputs (optional)
 };
+cudaError_t launch_wait_probe(Control *ctl, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s);
 cudaError_t launch_graph_energy(const GraphParams &p, int n_groups, cudaStream_t s);
 cudaError_t graph_prepare(int maxN);  // shared-memory limit of the graph kernels for N up to maxN
