@@ -143,6 +143,7 @@ struct LearnState {
     uint64_t seed = 0;
     float *P = nullptr, *Gr = nullptr, *Am = nullptr, *Av = nullptr, *M1 = nullptr, *M2 = nullptr, *M3 = nullptr;
     __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2T = nullptr, *W3T = nullptr;
+    __nv_bfloat16 *W1c = nullptr, *W2c = nullptr, *W3c = nullptr;  // canonical K-major copies (fused forward)
     float *du = nullptr, *dphi = nullptr, *dextra = nullptr;
     int *dcond = nullptr;
     __nv_bfloat16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *H2T = nullptr;
@@ -380,6 +381,18 @@ int learn_forward(pt_ctx *c, const __nv_bfloat16 *X, int rows, const int *cond, 
     LearnState &L = *c->learn;
     const ptgb::LearnShape &sh = L.sh;
     const int64_t rc = L.rows;
+    if (!train && rows <= 128) {  // sampling passes: the whole network in one launch, activations on chip
+        MlpParams m{};
+        m.X = X; m.strideX = rc * sh.Din; m.ldx = sh.Din; m.M = rows; m.Din = sh.Din; m.H = sh.H; m.Dout = sh.Dout;
+        m.W1c = L.W1c; m.W2c = L.W2c; m.W3c = L.W3c;
+        m.strideW1 = (int64_t)sh.H * sh.Din; m.strideW2 = (int64_t)sh.H * sh.H; m.strideW3 = (int64_t)sh.Dout * sh.H;
+        m.P = L.P; m.psize = (int64_t)sh.psize; m.ob1 = sh.ob1; m.oC1 = sh.oC1; m.ob2 = sh.ob2; m.ob3 = sh.ob3;
+        m.cond = cond; m.strideCond = strideCond;
+        m.O = L.O; m.strideO = rc * sh.Dout; m.ldo = sh.Dout;
+        m.err = &c->d_ctl->error;
+        CK(launch_fused_mlp(m, c->S, c->stream));
+        return PT_OK;
+    }
     GemmParams g{};
     g.A = X; g.strideA = rc * sh.Din; g.lda = sh.Din;
     g.B = L.W1; g.strideB = (int64_t)sh.H * sh.Din; g.ldb = sh.Din;
@@ -455,6 +468,7 @@ int learn_cast(pt_ctx *c) {
     CastParams cp{};
     cp.P = L.P; cp.M1 = L.M1; cp.M2 = L.M2; cp.M3 = L.M3;
     cp.W1 = L.W1; cp.W2 = L.W2; cp.W3 = L.W3; cp.W2T = L.W2T; cp.W3T = L.W3T; cp.sh = L.sh;
+    cp.W1c = L.W1c; cp.W2c = L.W2c; cp.W3c = L.W3c;
     CK(launch_cast(cp, c->stream));
     return PT_OK;
 }
@@ -1421,6 +1435,8 @@ int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_
     L->W1 = lalloc<__nv_bfloat16>(c, S * sh.H * sh.Din, &rc); L->W2 = lalloc<__nv_bfloat16>(c, S * sh.H * sh.H, &rc);
     L->W3 = lalloc<__nv_bfloat16>(c, S * sh.Dout * sh.H, &rc); L->W2T = lalloc<__nv_bfloat16>(c, S * sh.H * sh.H, &rc);
     L->W3T = lalloc<__nv_bfloat16>(c, S * sh.Dout * sh.H, &rc);
+    L->W1c = lalloc<__nv_bfloat16>(c, S * sh.H * sh.Din, &rc); L->W2c = lalloc<__nv_bfloat16>(c, S * sh.H * sh.H, &rc);
+    L->W3c = lalloc<__nv_bfloat16>(c, S * sh.Dout * sh.H, &rc);
     L->du = lalloc<float>(c, S * L->ncap * N, &rc); L->dphi = lalloc<float>(c, S * L->ncap * N, &rc);
     L->dextra = lalloc<float>(c, S * L->ncap, &rc); L->dcond = lalloc<int>(c, S * L->ncap, &rc);
     L->X = lalloc<__nv_bfloat16>(c, S * rows * sh.Din, &rc); L->XT = lalloc<__nv_bfloat16>(c, S * rows * sh.Din, &rc);

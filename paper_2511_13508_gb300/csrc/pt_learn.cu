@@ -138,20 +138,26 @@ __global__ void cast_kernel(CastParams p) {
     const float *P = p.P + (size_t)s * sh.psize;
     const size_t n1 = (size_t)sh.H * sh.Din, n2 = (size_t)sh.H * sh.H, n3 = (size_t)sh.Dout * sh.H;
     for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3; i += gridDim.x * blockDim.x) {
+        // canonical K-major position of element (n, k) of an N x K matrix: ((k / 8) N + n) 8 + k % 8
         if (i < n1) {
-            p.W1[s * n1 + i] = __float2bfloat16_rn(P[sh.oW1 + i] * p.M1[i]);
+            const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW1 + i] * p.M1[i]);
+            p.W1[s * n1 + i] = w;
+            const size_t n = i / sh.Din, k = i % sh.Din;
+            p.W1c[s * n1 + ((k / 8) * sh.H + n) * 8 + k % 8] = w;
         } else if (i < n1 + n2) {
             const size_t j = i - n1;
             const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW2 + j] * p.M2[j]);
             p.W2[s * n2 + j] = w;
             const size_t h2 = j / sh.H, h1 = j % sh.H;
             p.W2T[s * n2 + h1 * sh.H + h2] = w;
+            p.W2c[s * n2 + ((h1 / 8) * sh.H + h2) * 8 + h1 % 8] = w;
         } else {
             const size_t j = i - n1 - n2;
             const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW3 + j] * p.M3[j]);
             p.W3[s * n3 + j] = w;
             const size_t o = j / sh.H, h = j % sh.H;
             p.W3T[s * n3 + h * sh.Dout + o] = w;
+            p.W3c[s * n3 + ((h / 8) * sh.Dout + o) * 8 + h % 8] = w;
         }
     }
 }
@@ -428,7 +434,9 @@ __global__ void assemble_kernel(AssembleParams p) {
             sn = sf * inv;
             cs = cf * inv;
         }
-        p.a[grow * N + k] = make_double2(A * cs, A * sn);
+        // FP32 chains store the proposal rounded to FP32: its density and energy are taken of that rounding,
+        // the configuration the chain will hold
+        p.a[grow * N + k] = p.dbl ? make_double2(A * cs, A * sn) : make_double2((float)(A * cs), (float)(A * sn));
     }
 }
 
@@ -439,9 +447,13 @@ cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------------------
-__global__ void energy_list_kernel(EnergyListParams p) {
-    __shared__ double2 sa[512];
-    __shared__ double red[32];
+// FP64 energy H = -cc sum_q J_q Re(conj(a_x) a_y a_z conj(a_w)) of one row per block.  The pair products
+// P(x, y) = conj(a_x) a_y of the row are tabulated in shared memory first (N^2 entries), so that each term is
+// Re(P(x, y) conj(P(z, w))) times J_q: three FP64 operations per quadruplet instead of nine.
+__global__ void __launch_bounds__(256) energy_list_kernel(EnergyListParams p) {
+    extern __shared__ double2 pairs[];  // [N][N]
+    __shared__ double2 sa[kLearnMaxN];
+    __shared__ double red[8];
     const int s = blockIdx.y, row = blockIdx.x, N = p.N;
     const int64_t grow = (int64_t)s * p.rows_per_sample + row;
     const SampleDev sd = p.samples[s];
@@ -458,31 +470,42 @@ __global__ void energy_list_kernel(EnergyListParams p) {
         }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const double2 x = sa[e / N], y = sa[e % N];
+        pairs[e] = make_double2(x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x);
+    }
+    __syncthreads();
     const int4 *Q = p.quads + sd.q_off;
     const double *J = p.Jq + sd.q_off;
     double acc = 0.0;
     for (int64_t q = threadIdx.x; q < sd.nq; q += blockDim.x) {
         const int4 t = Q[q];
-        const double2 a = sa[t.x], b = sa[t.y], c = sa[t.z], d = sa[t.w];
-        // Re( conj(a) b c conj(d) )
-        const double xr = a.x * b.x + a.y * b.y, xi = a.x * b.y - a.y * b.x;   // conj(a) b
-        const double yr = c.x * d.x + c.y * d.y, yi = c.y * d.x - c.x * d.y;   // c conj(d)
-        acc += J[q] * (xr * yr - xi * yi);
+        const double2 u = pairs[t.x * N + t.y], w = pairs[t.z * N + t.w];
+        acc += J[q] * (u.x * w.x + u.y * w.y);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        for (int w = 0; w < 8; ++w) t += red[w];
         p.E[grow] = -p.cc * t;
     }
 }
 
 cudaError_t launch_energy_list(const EnergyListParams &p, int S, cudaStream_t s) {
     if (p.rows_per_sample <= 0) return cudaSuccess;
+    if (p.N < 1 || p.N > kLearnMaxN) return cudaErrorInvalidValue;
+    const size_t sm = sizeof(double2) * (size_t)p.N * p.N;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(energy_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(sizeof(double2) * kLearnMaxN * kLearnMaxN));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     dim3 grid(p.rows_per_sample, S);
-    energy_list_kernel<<<grid, 256, 0, s>>>(p);
+    energy_list_kernel<<<grid, 256, sm, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ namespace ptgb {
 
 constexpr uint32_t kTagGlobal = 5u, kTagBatch = 6u;
 constexpr int kLearnBlocks = 8;  // autoregressive blocks of modes
+constexpr int kLearnMaxN = 64;   // largest N of the proposal network
 
 struct LearnShape {
     int N, H, Din, Dout, ncold, S;
@@ -59,6 +60,7 @@ struct CastParams {
     const float *P;         // [S][psize]
     const float *M1, *M2, *M3;
     __nv_bfloat16 *W1, *W2, *W3, *W2T, *W3T;
+    __nv_bfloat16 *W1c, *W2c, *W3c;  // the same weights in the canonical K-major layout [K/8][N][8]
     LearnShape sh;
 };
 cudaError_t launch_cast(const CastParams &p, cudaStream_t s);

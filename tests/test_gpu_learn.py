@@ -140,6 +140,36 @@ def test_learn_eval_geometric_tails(N):
     assert np.allclose(lq[0], lq_o, rtol=1e-4, atol=2e-3), np.abs(lq[0] - lq_o).max()
 
 
+@pytest.mark.parametrize("N,rows", [(16, 1), (48, 72), (64, 128)])
+def test_learn_eval_single_launch_forward_matches_oracle(N, rows):
+    """Without a gradient and with at most 128 rows per sample the network runs as one fused launch (three
+    tcgen05 products, hidden activations in shared memory).  It must give the three-GEMM path's result bit for
+    bit (same products in the same K order, same epilogue arithmetic), and follow the FP64 oracle with the
+    BF16 rounding points emulated.  Against the oracle a hidden value that sits on a BF16 rounding boundary
+    can round the other way (the oracle rounds its FP64 value, the kernel its FP32 one); with these sharp
+    densities (|log q| ~ 1e3) one such flip moves log q by up to ~4e-5 |log q|, so 95% of the rows are held
+    to the usual bound and every row to that allowance."""
+    S, R, nT, ncold = 3, 4, 4, 3
+    pt = pkg.PT([N] * S, _couplings([N] * S), workload.geometric_ladder(0.5, 1.5, nT), R, 5, precision="fp32")
+    pt.learn_init(n_cold=ncold, batch=256, data_per_sample=256, seed=3)
+    sh = pt.learn_shape()
+    rng = np.random.default_rng(7 * N + rows)
+    P = _randomise_outputs(pt.learn_params().astype(np.float64), sh, rng).astype(np.float32)
+    pt.set_learn_params(P)
+    a = _dirichlet(N, (S, rows), 0.5, rng).astype(np.complex64).astype(np.complex128)
+    cond = rng.integers(0, ncold, (S, rows)).astype(np.int32)
+    lq, ex, _ = pt.learn_eval(a, cond)
+    if rows % 8 == 0:  # the gradient path takes whole groups of 8 rows
+        lq_g, ex_g, _ = pt.learn_eval(a, cond, grad=True)  # the three-GEMM path
+        assert np.array_equal(ex, ex_g) and np.array_equal(lq, lq_g)
+    for s in range(S):
+        lq_o, ex_o = ol.logq(P[s].astype(np.float64), a[s], cond[s], N, sh["H"], ncold, 8, emulate_bf16=True)
+        err = np.abs(lq[s] - lq_o)
+        scale = np.abs(lq_o).max()
+        assert np.quantile(err, 0.95) <= 2e-3 + 1e-5 * scale, (np.quantile(err, 0.95), scale)
+        assert err.max() <= 2e-3 + 5e-5 * scale, (err.max(), scale)
+
+
 def test_learn_eval_rejects_bad_arguments():
     S, N = 1, 16
     pt = pkg.PT([N], _couplings([N]), workload.geometric_ladder(0.5, 1.5, 2), 4, 1, precision="fp32")
@@ -277,6 +307,36 @@ def _trained(N, S, R, temps, ncold, seed, steps=4000):
     pt.collect(16, 1024)
     losses = pt.train(steps, lr=1e-3)
     return pt, losses
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_accepted_global_moves_carry_the_energy_of_the_stored_state(prec):
+    """Global moves alone (no sweeps in between): a chain that took a proposal must carry the FP64 energy
+    (oracle) of the configuration it now holds, computed by the proposal path (pair-product table in shared
+    memory); for FP32 chains that is the energy of the proposal as rounded to FP32, the configuration the
+    chain stores (the energy of the unrounded proposal differs by ~1e-8 here).  Chains that took none keep
+    their energy unchanged."""
+    import oracle
+    N, S, R, nT, ncold = 64, 2, 4, 4, 4
+    J = [0.05 * j for j in _couplings([N] * S)]
+    pt = pkg.PT([N] * S, J, workload.geometric_ladder(0.5, 1.5, nT), R, 31, precision=prec)
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
+    sh = pt.learn_shape()
+    pt.set_learn_params(_stick_breaking_biases(N, pt.learn_params().astype(np.float64), sh).astype(np.float32))
+    pt.set_global_blocks(5, 7)
+    a0, E0 = pt.state()
+    for _ in range(12):
+        pt.global_move()
+    a, E = pt.state()
+    moved = np.any(a.reshape(-1, N) != a0.reshape(-1, N), axis=1)
+    assert moved.sum() >= 8, moved.sum()
+    assert np.array_equal(E[~moved], E0[~moved])
+    quads = oracle.enumerate_quads(N)
+    a = a.reshape(S, R * nT, N)
+    for c in np.flatnonzero(moved):
+        s_, r_ = divmod(int(c), R * nT)
+        ref = oracle.energy(N, quads, J[s_], a[s_, r_])
+        assert abs(E[c] - ref) <= 1e-13 * np.abs(J[s_]).sum(), (c, E[c], ref)
 
 
 def test_training_lowers_the_nll_and_raises_acceptance():
