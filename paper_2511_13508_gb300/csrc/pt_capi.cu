@@ -498,10 +498,6 @@ int run_global(pt_ctx *c) {
     if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
     DensityParams dc = density_params(L, L.rcur, L.lq_cur, np, false);
     CK(launch_density(dc, c->S, c->stream));
-    EnergyListParams ep{};
-    ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
-    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
-    CK(launch_energy_list(ep, c->S, c->stream));
     // autoregressive sampling, one pass per block of modes from the first resampled block of each row on;
     // the blocks below it keep the current configuration's features and variables
     CK(cudaMemcpyAsync(L.Xp, L.X, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din, cudaMemcpyDeviceToDevice,
@@ -531,9 +527,15 @@ int run_global(pt_ctx *c) {
     if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
     DensityParams dq = density_params(L, L.rprop, L.lq_prop, np, false);
     CK(launch_density(dq, c->S, c->stream));
-    EnergyListParams eq = ep;
+    // exact FP64 energies of the current configurations and of the proposals, one launch
+    EnergyList2 el{};
+    EnergyListParams &ep = el.set[0];
+    ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
+    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
+    EnergyListParams &eq = el.set[1];
+    eq = ep;
     eq.a = L.a_prop; eq.dbl = 1; eq.slot = nullptr; eq.E = L.H_prop;
-    CK(launch_energy_list(eq, c->S, c->stream));
+    CK(launch_energy_list(el, 2, c->S, c->stream));
     MHParams mp{};
     mp.logq_cur = L.lq_cur; mp.logq_prop = L.lq_prop; mp.H_cur = L.H_cur; mp.H_prop = L.H_prop;
     mp.extra_cur = L.rcur.extra; mp.extra_prop = L.rprop.extra; mp.a_prop = L.a_prop; mp.a = c->d_a;

@@ -232,25 +232,24 @@ __global__ void __launch_bounds__(128, 2) gemm_bf16_tc_kernel(GemmParams p) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Fused forward pass of the proposal network (see MlpParams), one thread block per sample.
-//  - Weights arrive pre-arranged in the canonical K-major layout ([K/8][N][8] BF16, written by the cast
-//    kernel), so one K-chunk of 64 (8 K-groups x N rows, up to 32 KB) is one contiguous bulk copy into a ring of
-//    weight stages.  One thread issues the copies and the MMAs of all three layers in order; the copies of
-//    later chunks (also of the next layers) stay in flight while the tensor cores consume earlier ones.
-//  - Activations (input, H1, H2) live in shared memory in the canonical layout with a K-group stride of
-//    Mp x 16 bytes (Mp = rows rounded up to 16).  The MMA always reads 128 rows; rows >= Mp read whatever
-//    follows (each buffer is padded so that this stays inside the block's shared memory) and only produce
-//    accumulator lanes that nobody reads.
-//  - The accumulator of each layer occupies the same 256 TMEM columns; 16 warps read it back (warp w: TMEM
-//    lanes 32 (w % 4) .., columns split four ways), add the biases, apply the ReLU and write the next layer's
-//    BF16 input, or the FP32 outputs.
+// Fused forward pass of the proposal network (see MlpParams): a cluster of kMlpCL thread blocks per sample,
+// block r computing output columns [r N/kMlpCL, (r+1) N/kMlpCL) of every layer.
+//  - Weights arrive in the sliced canonical layout (written by the cast kernel): block r's rows of a layer
+//    are one contiguous run, loaded by a single bulk copy.  All three slices (at most 96 KB) are requested
+//    at the start, so the copies overlap the input staging and the earlier layers.
+//  - Activations (input, H1, H2) are held whole (all 256 K columns, Mp = rows rounded up to 16) in every
+//    block, in the canonical layout with a K-group stride of Mp x 16 bytes.  The MMA reads 128 rows; rows
+//    >= Mp read whatever follows (each buffer is padded so that this stays inside the block's shared memory)
+//    and only produce accumulator lanes nobody reads.
+//  - After a hidden layer each block writes its BF16 column slice of relu(acc + b (+ C1[cond])) into the next
+//    activation buffer of all blocks of the cluster (distributed shared memory); a cluster barrier makes the
+//    writes visible before the next layer's MMAs.
+//  - 8 warps read the accumulator back: warp w takes TMEM lanes 32 (w % 4).. and half of the slice's columns.
 namespace {
 
-constexpr int kMlpThreads = 512;
-constexpr int kMlpKC = 64;                          // K per chunk (8 K-groups)
-constexpr uint32_t kMlpStage = 256 * kMlpKC * 2;   // largest chunk: 256 rows x 64 K
-constexpr int kMlpMaxStages = 6;
-constexpr uint32_t kMlpPad = 2048;                 // rows Mp..127 of the last K-group
+constexpr int kMlpCL = 4;         // blocks per sample (cluster size)
+constexpr int kMlpThreads = 256;
+constexpr uint32_t kMlpPad = 2048;  // rows Mp..127 of the last K-group
 
 // rows [0, rows) (rows % 16 == 0) x K-groups [g0, g0 + groups) (groups even) of a row-major BF16 matrix into
 // the canonical layout at dst; rows >= nrows are zero-filled
@@ -292,218 +291,187 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The chunk sequence of the three layers: layer l has ceil(K_l / 64) chunks of W_l (N_l rows).
-struct MlpChunks {
-    const unsigned char *W[3];
-    int N[3], K[3], first[3], total;
-    __device__ int layer_of(int g) const { return g >= first[2] ? 2 : (g >= first[1] ? 1 : 0); }
-    __device__ uint32_t bytes(int g, int *groups) const {
-        const int l = layer_of(g), c = g - first[l];
-        *groups = min(kMlpKC, K[l] - c * kMlpKC) / 8;
-        return (uint32_t)(*groups) * (uint32_t)N[l] * 16u;
-    }
-    __device__ const unsigned char *src(int g) const {
-        const int l = layer_of(g), c = g - first[l];
-        return W[l] + (size_t)c * 8 * N[l] * 16;
-    }
-};
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-// Epilogue of a hidden layer: relu(acc + bias (+ cbias[cond[row]])) as BF16 into the activation buffer.
-__device__ void mlp_hidden_epilogue(uint32_t tmem, unsigned char *dst, uint32_t lboA, int Mp, int N, int M,
-                                    const float *bias, const float *cbias, const int *cond) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, quad = warp % 4, part = warp / 4;
-    const int row = quad * 32 + lane;
-    if (quad * 32 >= Mp) return;  // the whole warp's rows are padding
-    const bool live = row < M;
-    const float *cb = (cbias && live) ? cbias + (int64_t)cond[row] * N : nullptr;
-    const int span = N / 4;  // columns of this warp: [part * span, (part + 1) * span), span a multiple of 8
-    for (int c0 = part * span; c0 < (part + 1) * span; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-        const int ncol = min(32, (part + 1) * span - c0);
-        if (row < Mp) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (8 * g >= ncol) break;
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float v0 = 0.f, v1 = 0.f;
-                    if (live) {
-                        const int k0 = c0 + 8 * g + 2 * e;
-                        v0 = __uint_as_float(r[8 * g + 2 * e]) + bias[k0];
-                        v1 = __uint_as_float(r[8 * g + 2 * e + 1]) + bias[k0 + 1];
-                        if (cb) { v0 += cb[k0]; v1 += cb[k0 + 1]; }
-                        v0 = fmaxf(v0, 0.f);
-                        v1 = fmaxf(v1, 0.f);
-                    }
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                    w[e] = *reinterpret_cast<const uint32_t *>(&h);
-                }
-                *reinterpret_cast<uint4 *>(dst + (uint32_t)((c0 + 8 * g) / 8) * lboA + (uint32_t)row * 16) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
+// 16 bytes to the same shared-memory offset in block `rank` of the cluster
+__device__ __forceinline__ void st_cluster16(uint32_t local, uint32_t rank, uint4 v) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(remote), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+// One layer's products: TMEM[0..NS) = act (128 x K) * Wslice^T, issued by one thread, completion on `done`.
+__device__ __forceinline__ void mlp_mma(uint32_t tmem, uint32_t abuf, uint32_t lboA, uint32_t wbuf, int NS, int K,
+                                       uint64_t *done) {
+    const uint32_t idesc = make_idesc(NS), lboB = (uint32_t)NS * 16u;
+    for (int t = 0; t < K / 16; ++t) {
+        const uint64_t da = make_sdesc(abuf + (uint32_t)(2 * t) * lboA, lboA, 128);
+        const uint64_t db = make_sdesc(wbuf + (uint32_t)(2 * t) * lboB, lboB, 128);
+        const uint32_t acc = t > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred pacc;\n\tsetp.ne.b32 pacc, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pacc;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
     }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(done))
+                 : "memory");
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kMlpThreads, 1) fused_mlp_kernel(MlpParams p, int n_stages) {
+__global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1) fused_mlp_kernel(MlpParams p) {
     extern __shared__ __align__(1024) unsigned char msm[];
-    __shared__ uint64_t full[kMlpMaxStages], empty[kMlpMaxStages], done;
+    __shared__ uint64_t full[3], done;
     __shared__ uint32_t tmem_base_slot;
-    const int b = blockIdx.x, warp = threadIdx.x / 32;
+    __shared__ float bsl[3][64];  // this block's slices of b1, b2, b3
+    const uint32_t rank = cluster_rank();
+    const int b = blockIdx.x / kMlpCL, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int NS = p.H / kMlpCL, NS3 = p.Dout / kMlpCL;
     const int Mp = (p.M + 15) & ~15;
     const uint32_t lboA = (uint32_t)Mp * 16u;
-    const uint32_t act_bytes = 32u * lboA + kMlpPad;  // 256 columns
-    unsigned char *act0 = msm, *act1 = msm + act_bytes;
-    const uint32_t sAct0 = smem_addr(act0), sAct1 = smem_addr(act1), sW = smem_addr(msm + 2 * act_bytes);
-    MlpChunks ch;
-    ch.W[0] = reinterpret_cast<const unsigned char *>(p.W1c + (int64_t)b * p.strideW1);
-    ch.W[1] = reinterpret_cast<const unsigned char *>(p.W2c + (int64_t)b * p.strideW2);
-    ch.W[2] = reinterpret_cast<const unsigned char *>(p.W3c + (int64_t)b * p.strideW3);
-    ch.N[0] = p.H; ch.N[1] = p.H; ch.N[2] = p.Dout;
-    ch.K[0] = p.Din; ch.K[1] = p.H; ch.K[2] = p.H;
-    ch.first[0] = 0;
-    ch.first[1] = (p.Din + kMlpKC - 1) / kMlpKC;
-    ch.first[2] = ch.first[1] + (p.H + kMlpKC - 1) / kMlpKC;
-    ch.total = ch.first[2] + (p.H + kMlpKC - 1) / kMlpKC;
+    const uint32_t act_bytes = 32u * lboA + kMlpPad;  // 256 K columns
+    const uint32_t sAct0 = smem_addr(msm), sAct1 = sAct0 + act_bytes;
+    const uint32_t wbytes[3] = {(uint32_t)p.Din * NS * 2u, (uint32_t)p.H * NS * 2u, (uint32_t)p.H * NS3 * 2u};
+    const uint32_t sW[3] = {sAct1 + act_bytes, sAct1 + act_bytes + wbytes[0], sAct1 + act_bytes + wbytes[0] + wbytes[1]};
+    const unsigned char *gW[3] = {
+        reinterpret_cast<const unsigned char *>(p.W1c + (int64_t)b * p.strideW1) + (size_t)rank * wbytes[0],
+        reinterpret_cast<const unsigned char *>(p.W2c + (int64_t)b * p.strideW2) + (size_t)rank * wbytes[1],
+        reinterpret_cast<const unsigned char *>(p.W3c + (int64_t)b * p.strideW3) + (size_t)rank * wbytes[2]};
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_base_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&tmem_base_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < n_stages; ++i) { mbar_init1(&full[i]); mbar_init1(&empty[i]); }
+        for (int l = 0; l < 3; ++l) mbar_init1(&full[l]);
         mbar_init1(&done);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    // the first chunks of the weights, then the input rows (rows M..Mp-1 zero)
     if (threadIdx.x == 0)
-        for (int g = 0; g < min(n_stages, ch.total); ++g) {
-            int groups;
-            const uint32_t nb = ch.bytes(g, &groups);
-            mbar_expect_tx(&full[g], nb);
-            bulk_g2s(sW + g * kMlpStage, ch.src(g), nb, &full[g]);
+        for (int l = 0; l < 3; ++l) {
+            mbar_expect_tx(&full[l], wbytes[l]);
+            bulk_g2s(sW[l], gW[l], wbytes[l], &full[l]);
         }
+    const float *P = p.P + (int64_t)b * p.psize;
+    if (threadIdx.x < 64) {
+        bsl[0][threadIdx.x] = P[p.ob1 + rank * NS + threadIdx.x];
+        bsl[1][threadIdx.x] = P[p.ob2 + rank * NS + threadIdx.x];
+        bsl[2][threadIdx.x] = threadIdx.x < NS3 ? P[p.ob3 + rank * NS3 + threadIdx.x] : 0.f;
+    }
     stage_rows(sAct0, p.X + (int64_t)b * p.strideX, p.ldx, Mp, p.M, 0, p.Din / 8, lboA);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    cluster_arrive();  // this block runs: the others may write into its shared memory once they have waited
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_slot;
-    const float *P = p.P + (int64_t)b * p.psize;
     const int *cond = p.cond + (int64_t)b * p.strideCond;
+    const int quad = warp % 4, part = warp / 4, row = quad * 32 + lane;
     bool ok = true;
-    int issued = min(n_stages, ch.total);
     for (int l = 0; l < 3; ++l) {
-        const uint32_t abuf = (l == 1) ? sAct1 : sAct0;  // x -> H1 (act1) -> H2 (act0)
+        const int nsl = l < 2 ? NS : NS3;
         if (threadIdx.x == 0) {
-            const uint32_t idesc = make_idesc(ch.N[l]);
-            const uint32_t lboB = (uint32_t)ch.N[l] * 16u;
-            for (int g = ch.first[l]; g < (l < 2 ? ch.first[l + 1] : ch.total) && ok; ++g) {
-                const int st = g % n_stages;
-                if (!mbar_wait(&full[st], (uint32_t)(g / n_stages) & 1u)) { ok = false; break; }
+            if (mbar_wait(&full[l], 0u)) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                int groups;
-                ch.bytes(g, &groups);
-                const int c = g - ch.first[l];
-                for (int t = 0; t < groups / 2; ++t) {
-                    const uint64_t da = make_sdesc(abuf + (uint32_t)(c * 8 + 2 * t) * lboA, lboA, 128);
-                    const uint64_t db = make_sdesc(sW + st * kMlpStage + 2 * t * lboB, lboB, 128);
-                    const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred pacc;\n\tsetp.ne.b32 pacc, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pacc;\n\t}" ::"r"(tmem),
-                        "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                        : "memory");
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_addr(&empty[st]))
-                             : "memory");
-                // refill the stage of the previous chunk once its MMAs are done
-                if (g >= 1 && issued < ch.total) {
-                    const int gp = g - 1, sp = gp % n_stages;
-                    if (!mbar_wait(&empty[sp], (uint32_t)(gp / n_stages) & 1u)) { ok = false; break; }
-                    int gr;
-                    const uint32_t nb = ch.bytes(issued, &gr);
-                    mbar_expect_tx(&full[sp], nb);
-                    bulk_g2s(sW + sp * kMlpStage, ch.src(issued), nb, &full[sp]);
-                    ++issued;
-                }
+                mlp_mma(tmem, l == 1 ? sAct1 : sAct0, lboA, sW[l], nsl, l == 0 ? p.Din : p.H, &done);
+            } else {
+                ok = false;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&done))
-                         : "memory");
         }
         __syncwarp();
         if (!mbar_wait(&done, (uint32_t)l & 1u)) ok = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;
-        if (!ok) break;
+        // every block takes part in every cluster barrier, whatever its status, so that none waits forever
+        const int span = nsl / 2, c0 = part * span, ncol = min(32, span);
+        uint32_t r[32];
+        if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
         if (l < 2) {
-            mlp_hidden_epilogue(tmem, l == 0 ? act1 : act0, lboA, Mp, p.H, p.M, P + (l == 0 ? p.ob1 : p.ob2),
-                                l == 0 ? P + p.oC1 : nullptr, l == 0 ? cond : nullptr);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        } else {
-            const int lane = threadIdx.x % 32, quad = warp % 4, part = warp / 4;
-            const int row = quad * 32 + lane, span = p.Dout / 4;
-            if (quad * 32 < Mp) {
-                const float *b3 = P + p.ob3;
-                for (int c0 = part * span; c0 < (part + 1) * span; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-                    const int ncol = min(32, (part + 1) * span - c0);
-                    if (row < p.M) {
-                        float *o = p.O + (int64_t)b * p.strideO + (int64_t)row * p.ldo + c0;
+            if (l == 0) cluster_wait();  // all blocks of the cluster have started
+            if (quad * 32 < Mp && row < Mp && ok) {
+                const bool live = row < p.M;
+                const float *cb = (l == 0 && live) ? P + p.oC1 + (int64_t)cond[row] * p.H + rank * NS + c0 : nullptr;
+                float cv[32];
 #pragma unroll
-                        for (int q = 0; q < 32; q += 4)
-                            if (q < ncol)
-                                *reinterpret_cast<float4 *>(o + q) = make_float4(
-                                    __uint_as_float(r[q]) + b3[c0 + q], __uint_as_float(r[q + 1]) + b3[c0 + q + 1],
-                                    __uint_as_float(r[q + 2]) + b3[c0 + q + 2], __uint_as_float(r[q + 3]) + b3[c0 + q + 3]);
+                for (int q = 0; q < 32; ++q) cv[q] = (cb && q < ncol) ? cb[q] : 0.f;
+                const uint32_t dst = (l == 0 ? sAct1 : sAct0) + (uint32_t)row * 16u;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (8 * g >= ncol) break;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = 8 * g + 2 * e;
+                        float v0 = __uint_as_float(r[q]) + bsl[l][c0 + q] + cv[q];
+                        float v1 = __uint_as_float(r[q + 1]) + bsl[l][c0 + q + 1] + cv[q + 1];
+                        v0 = live ? fmaxf(v0, 0.f) : 0.f;
+                        v1 = live ? fmaxf(v1, 0.f) : 0.f;
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                        w[e] = *reinterpret_cast<const uint32_t *>(&h);
                     }
+                    const uint32_t kg = (uint32_t)(rank * NS + c0 + 8 * g) / 8;
+                    const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
+                    for (uint32_t dstr = 0; dstr < (uint32_t)kMlpCL; ++dstr) st_cluster16(dst + kg * lboA, dstr, v);
                 }
             }
+            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");  // generic writes -> tensor core reads
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            cluster_arrive();
+            cluster_wait();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        } else if (quad * 32 < Mp && row < p.M && ok) {
+            float *o = p.O + (int64_t)b * p.strideO + (int64_t)row * p.ldo + rank * NS3 + c0;
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+                if (q < ncol)
+                    *reinterpret_cast<float4 *>(o + q) =
+                        make_float4(__uint_as_float(r[q]) + bsl[2][c0 + q], __uint_as_float(r[q + 1]) + bsl[2][c0 + q + 1],
+                                    __uint_as_float(r[q + 2]) + bsl[2][c0 + q + 2],
+                                    __uint_as_float(r[q + 3]) + bsl[2][c0 + q + 3]);
         }
     }
     if (!ok && threadIdx.x == 0) {
         if (p.err) atomicCAS(p.err, 0, kErrTimeout);
         // let the bulk copies still in flight land before the block's shared memory is released
-        for (int g = 0; g < issued; ++g) (void)mbar_wait(&full[g % n_stages], (uint32_t)(g / n_stages) & 1u);
+        for (int l = 0; l < 3; ++l) (void)mbar_wait(&full[l], 0u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 cudaError_t launch_fused_mlp(const MlpParams &p, int batch, cudaStream_t s) {
-    // M <= 128 rows, Din a multiple of 16 (<= 256), H = 256, Dout a multiple of 32 (<= 256), 16-byte aligned
-    // canonical weights, O rows 16-byte aligned
-    if (p.M < 1 || p.M > 128 || p.Din < 16 || p.Din > 256 || (p.Din % 16) || p.H != 256 || p.Dout < 32 ||
-        p.Dout > 256 || (p.Dout % 32) || (p.ldo % 4) || batch < 1 || !p.W1c || !p.W2c || !p.W3c ||
+    // M <= 128 rows; Din a multiple of 16 (<= 192); H = 256; Dout/4 a multiple of 16 (<= 64); 16-byte aligned
+    // weights; O rows 16-byte aligned
+    if (p.M < 1 || p.M > 128 || p.Din < 16 || p.Din > 192 || (p.Din % 16) || p.H != 256 || p.Dout < 64 ||
+        p.Dout > 256 || (p.Dout % 64) || (p.ldo % 4) || batch < 1 || !p.W1c || !p.W2c || !p.W3c ||
         ((uintptr_t)p.W1c | (uintptr_t)p.W2c | (uintptr_t)p.W3c) % 16 ||
         ((p.strideW1 | p.strideW2 | p.strideW3) * 2) % 16)
         return cudaErrorInvalidValue;
-    constexpr size_t kSmemMax = 227 * 1024 - 1024;  // minus the static part
     const int Mp = (p.M + 15) & ~15;
     const size_t act = 2 * (32 * (size_t)Mp * 16 + kMlpPad);
-    const int n_stages = (int)std::min<size_t>(kMlpMaxStages, (kSmemMax - act) / kMlpStage);
-    if (n_stages < 2) return cudaErrorInvalidValue;
-    const size_t sm = act + (size_t)n_stages * kMlpStage;
+    const size_t w = ((size_t)p.Din + p.H) * (p.H / kMlpCL) * 2 + (size_t)p.H * (p.Dout / kMlpCL) * 2;
+    const size_t sm = act + w;
+    constexpr size_t kSmemMax = 227 * 1024 - 2048;  // minus the static part
+    if (sm > kSmemMax) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(fused_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    fused_mlp_kernel<<<batch, kMlpThreads, sm, s>>>(p, n_stages);
+    fused_mlp_kernel<<<batch * kMlpCL, kMlpThreads, sm, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -39,15 +39,16 @@ struct GemmParams {
 
 cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s);
 
-// The proposal network's whole forward pass for up to 128 rows per sample in one thread block:
+// The proposal network's whole forward pass for up to 128 rows per sample in one launch:
 // O = W3 relu(W2 relu(W1 x + b1 + C1[cond]) + b2) + b3, the hidden activations kept in shared memory (BF16)
-// and every product on the tensor cores.  One block per sample (batch = samples).
+// and every product on the tensor cores.  One cluster of four thread blocks per sample (batch = samples).
 struct MlpParams {
     const __nv_bfloat16 *X;  // [batch][rows of stride ldx] inputs, row-major (Din columns)
     int64_t strideX;
     int ldx, M, Din, H, Dout;
-    // masked BF16 weights per sample in the canonical K-major layout [K/8][N][8] (element (n, k) at
-    // ((k / 8) N + n) 8 + k % 8): W1 (N = H, K = Din), W2 (H, H), W3 (Dout, H)
+    // masked BF16 weights per sample in the sliced canonical K-major layout: for an N x K matrix cut into four
+    // slices of NS = N/4 rows, element (n, k) at ((n / NS) (K / 8) + k / 8) NS 8 + (n % NS) 8 + k % 8, so that
+    // each slice is contiguous: W1 (N = H, K = Din), W2 (H, H), W3 (Dout, H)
     const __nv_bfloat16 *W1c, *W2c, *W3c;
     int64_t strideW1, strideW2, strideW3;
     const float *P;          // FP32 master parameters [batch][psize]: biases b1, C1, b2, b3

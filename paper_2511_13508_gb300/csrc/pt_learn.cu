@@ -2,6 +2,7 @@
 // density and its gradient with respect to the network outputs, bias gradients, Adam, block-wise
 // sampling, assembly of proposed configurations, FP64 energies and the exact Metropolis-Hastings step.
 // The dense layers run on the tensor cores (pt_gemm.cu).  See pt_learn.h for the density.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include "pt_common.cuh"
@@ -90,20 +91,34 @@ __global__ void features_kernel(FeatParams p) {
         Rex[0] = (lane < 31 ? n0 : 0.0) + top;
         Rex[1] = lane < 31 ? n1 : 0.0;
     }
-    // phases, gauge fixed
-    const double ph0 = __shfl_sync(0xffffffffu, atan2(im[0], re[0]), 0);
-    const double ph1 = __shfl_sync(0xffffffffu, atan2(im[0], re[0]), 1);
+    // phases, gauge fixed.  The gauge phases phi_0 and phi_1 enter phi~_k k-fold and are taken in FP64; the
+    // others need only the FP32 accuracy the stored phi~_k has.  log R_{k+1} is the next mode's log R_k.
+    double phk[2], lr[2], ls[2];
+    for (int q = 0; q < 2; ++q) {
+        const int k = lane + 32 * q;
+        phk[q] = k < 2 ? atan2(im[q], re[q]) : (double)atan2f((float)im[q], (float)re[q]);
+        lr[q] = log(fmax(Rin[q], 1e-300));
+        ls[q] = log(sk[q]);
+    }
+    const double ph0 = __shfl_sync(0xffffffffu, phk[0], 0);
+    const double ph1 = __shfl_sync(0xffffffffu, phk[0], 1);
+    double lr1[2];
+    {
+        const double n0 = __shfl_down_sync(0xffffffffu, lr[0], 1), n1 = __shfl_down_sync(0xffffffffu, lr[1], 1);
+        const double b1 = __shfl_sync(0xffffffffu, lr[1], 0);  // log R_32
+        lr1[0] = lane < 31 ? n0 : b1;
+        lr1[1] = lane < 31 ? n1 : 0.0;  // k = 63 has no u
+    }
     double extra = 0.0;
     const int64_t rrow = (int64_t)s * p.raw_stride + p.raw_off + row;
     for (int q = 0; q < 2; ++q) {
         const int k = lane + 32 * q;
         if (k >= N) continue;
-        const double Rk = Rin[q], Rk1 = Rex[q];
-        const float u = (k <= N - 2) ? (float)(log(sk[q]) - log(fmax(Rk1, 1e-300))) : 0.f;
+        const float u = (k <= N - 2) ? (float)(ls[q] - (k + 1 < N ? lr1[q] : log(fmax(Rex[q], 1e-300)))) : 0.f;
         float ph = 0.f;
-        if (k >= 2) ph = wrap2pi((float)(atan2(im[q], re[q]) - ph0 - (double)k * (ph1 - ph0)));
-        if (k <= N - 2) extra -= log(fmax(Rk, 1e-300));
-        extra += 0.5 * log(sk[q]);
+        if (k >= 2) ph = wrap2pi((float)(phk[q] - ph0 - (double)k * (ph1 - ph0)));
+        if (k <= N - 2) extra -= lr[q];
+        extra += 0.5 * ls[q];
         p.raw.u[rrow * N + k] = u;
         p.raw.phi[rrow * N + k] = ph;
         if (p.X) {
@@ -126,38 +141,43 @@ __global__ void features_kernel(FeatParams p) {
 
 cudaError_t launch_features(const FeatParams &p, int S, cudaStream_t s) {
     if (p.rows_per_sample <= 0) return cudaSuccess;
-    dim3 grid((p.rows_per_sample + 3) / 4, S);
-    features_kernel<<<grid, 128, 0, s>>>(p);
+    dim3 grid((p.rows_per_sample + 1) / 2, S);  // two rows per block: the FP64 work spread over many SMs
+    features_kernel<<<grid, 64, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------------
+// Position of element (n, k) of an N x K matrix in the sliced canonical K-major layout: four slices of
+// NS = N/4 rows, each [K/8][NS][8] and contiguous.
+__device__ __forceinline__ size_t sliced_canonical(size_t n, size_t k, size_t N, size_t K) {
+    const size_t NS = N / 4;
+    return ((n / NS) * (K / 8) + k / 8) * NS * 8 + (n % NS) * 8 + k % 8;
+}
+
 __global__ void cast_kernel(CastParams p) {
     const LearnShape &sh = p.sh;
     const int s = blockIdx.y;
     const float *P = p.P + (size_t)s * sh.psize;
     const size_t n1 = (size_t)sh.H * sh.Din, n2 = (size_t)sh.H * sh.H, n3 = (size_t)sh.Dout * sh.H;
     for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3; i += gridDim.x * blockDim.x) {
-        // canonical K-major position of element (n, k) of an N x K matrix: ((k / 8) N + n) 8 + k % 8
         if (i < n1) {
             const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW1 + i] * p.M1[i]);
             p.W1[s * n1 + i] = w;
-            const size_t n = i / sh.Din, k = i % sh.Din;
-            p.W1c[s * n1 + ((k / 8) * sh.H + n) * 8 + k % 8] = w;
+            p.W1c[s * n1 + sliced_canonical(i / sh.Din, i % sh.Din, sh.H, sh.Din)] = w;
         } else if (i < n1 + n2) {
             const size_t j = i - n1;
             const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW2 + j] * p.M2[j]);
             p.W2[s * n2 + j] = w;
             const size_t h2 = j / sh.H, h1 = j % sh.H;
             p.W2T[s * n2 + h1 * sh.H + h2] = w;
-            p.W2c[s * n2 + ((h1 / 8) * sh.H + h2) * 8 + h1 % 8] = w;
+            p.W2c[s * n2 + sliced_canonical(h2, h1, sh.H, sh.H)] = w;
         } else {
             const size_t j = i - n1 - n2;
             const __nv_bfloat16 w = __float2bfloat16_rn(P[sh.oW3 + j] * p.M3[j]);
             p.W3[s * n3 + j] = w;
             const size_t o = j / sh.H, h = j % sh.H;
             p.W3T[s * n3 + h * sh.Dout + o] = w;
-            p.W3c[s * n3 + ((h / 8) * sh.Dout + o) * 8 + h % 8] = w;
+            p.W3c[s * n3 + sliced_canonical(o, h, sh.Dout, sh.H)] = w;
         }
     }
 }
@@ -447,14 +467,26 @@ cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// FP64 energy H = -cc sum_q J_q Re(conj(a_x) a_y a_z conj(a_w)) of one row per block.  The pair products
-// P(x, y) = conj(a_x) a_y of the row are tabulated in shared memory first (N^2 entries), so that each term is
-// Re(P(x, y) conj(P(z, w))) times J_q: three FP64 operations per quadruplet instead of nine.
-__global__ void __launch_bounds__(256) energy_list_kernel(EnergyListParams p) {
-    extern __shared__ double2 pairs[];  // [N][N]
+// Index of the pair (x, y), x < y, in the row-by-row upper triangle of an N x N table.
+__device__ __forceinline__ int tri_index(int x, int y, int N) { return x * (2 * N - x - 1) / 2 + (y - x - 1); }
+
+// FP64 energy H = -cc sum_q J_q Re(conj(a_x) a_y a_z conj(a_w)) of one row per block; blockIdx.z picks one
+// of two row sets (the current configurations and the proposals of a round, in one launch).
+//  - The pair products P(x, y) = conj(a_x) a_y, x < y, are tabulated in shared memory (upper triangle,
+//    N(N-1)/2 entries, 31.5 KB at N = 64, so that the launch's blocks fit on the GPU in one wave); a pair given
+//    in the other order is the conjugate, a sign flip done on the bits.  Each term is then
+//    J_q Re(P(x, y) conj P(z, w)): three FP64 operations per quadruplet instead of nine, which matters on a part
+//    whose FP64 rate is a small fraction of its FP32 rate.
+//  - Summing runs of quadruplets that share their first pair before multiplying by P(x, y) would save another
+//    third of the operations, but the run boundaries differ between the lanes of a warp and the divergent
+//    flushes cost the whole warp: it measured slower.
+__global__ void __launch_bounds__(256) energy_list_kernel(EnergyList2 pp) {
+    extern __shared__ double2 pairs[];  // [N (N - 1) / 2]
     __shared__ double2 sa[kLearnMaxN];
     __shared__ double red[8];
+    const EnergyListParams &p = pp.set[blockIdx.z];
     const int s = blockIdx.y, row = blockIdx.x, N = p.N;
+    if (row >= p.rows_per_sample) return;
     const int64_t grow = (int64_t)s * p.rows_per_sample + row;
     const SampleDev sd = p.samples[s];
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -470,9 +502,12 @@ __global__ void __launch_bounds__(256) energy_list_kernel(EnergyListParams p) {
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const double2 x = sa[e / N], y = sa[e % N];
-        pairs[e] = make_double2(x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x);
+    for (int e = threadIdx.x; e < N * (N - 1) / 2; e += blockDim.x) {
+        int x = 0, rem = e;  // e -> (x, y), x < y
+        while (rem >= N - 1 - x) { rem -= N - 1 - x; ++x; }
+        const int y = x + 1 + rem;
+        const double2 ax = sa[x], ay = sa[y];
+        pairs[e] = make_double2(ax.x * ay.x + ax.y * ay.y, ax.x * ay.y - ax.y * ay.x);
     }
     __syncthreads();
     const int4 *Q = p.quads + sd.q_off;
@@ -480,8 +515,12 @@ __global__ void __launch_bounds__(256) energy_list_kernel(EnergyListParams p) {
     double acc = 0.0;
     for (int64_t q = threadIdx.x; q < sd.nq; q += blockDim.x) {
         const int4 t = Q[q];
-        const double2 u = pairs[t.x * N + t.y], w = pairs[t.z * N + t.w];
-        acc += J[q] * (u.x * w.x + u.y * w.y);
+        const bool f1 = t.x > t.y, f2 = t.z > t.w;
+        const double2 u = pairs[f1 ? tri_index(t.y, t.x, N) : tri_index(t.x, t.y, N)];
+        const double2 w = pairs[f2 ? tri_index(t.w, t.z, N) : tri_index(t.z, t.w, N)];
+        // Im P(x, y) Im P(z, w) changes sign when exactly one of the two pairs was stored the other way round
+        const double wy = __longlong_as_double(__double_as_longlong(w.y) ^ ((long long)(f1 != f2) << 63));
+        acc = fma(J[q], fma(u.x, w.x, u.y * wy), acc);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
@@ -493,18 +532,15 @@ __global__ void __launch_bounds__(256) energy_list_kernel(EnergyListParams p) {
     }
 }
 
-cudaError_t launch_energy_list(const EnergyListParams &p, int S, cudaStream_t s) {
-    if (p.rows_per_sample <= 0) return cudaSuccess;
-    if (p.N < 1 || p.N > kLearnMaxN) return cudaErrorInvalidValue;
-    const size_t sm = sizeof(double2) * (size_t)p.N * p.N;
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(energy_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(sizeof(double2) * kLearnMaxN * kLearnMaxN));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+cudaError_t launch_energy_list(const EnergyList2 &p, int n_sets, int S, cudaStream_t s) {
+    int rows = 0;
+    for (int i = 0; i < n_sets; ++i) {
+        if (p.set[i].N < 1 || p.set[i].N > kLearnMaxN || p.set[i].N != p.set[0].N) return cudaErrorInvalidValue;
+        rows = std::max(rows, p.set[i].rows_per_sample);
     }
-    dim3 grid(p.rows_per_sample, S);
+    if (rows <= 0) return cudaSuccess;
+    const size_t sm = sizeof(double2) * (size_t)p.set[0].N * (p.set[0].N - 1) / 2;
+    dim3 grid(rows, S, n_sets);
     energy_list_kernel<<<grid, 256, sm, s>>>(p);
     return cudaGetLastError();
 }

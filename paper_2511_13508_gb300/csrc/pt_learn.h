@@ -60,7 +60,7 @@ struct CastParams {
     const float *P;         // [S][psize]
     const float *M1, *M2, *M3;
     __nv_bfloat16 *W1, *W2, *W3, *W2T, *W3T;
-    __nv_bfloat16 *W1c, *W2c, *W3c;  // the same weights in the canonical K-major layout [K/8][N][8]
+    __nv_bfloat16 *W1c, *W2c, *W3c;  // the same weights in the sliced canonical K-major layout (MlpParams)
     LearnShape sh;
 };
 cudaError_t launch_cast(const CastParams &p, cudaStream_t s);
@@ -154,7 +154,10 @@ struct EnergyListParams {
     double cc;
     double *E;               // [S][rows]
 };
-cudaError_t launch_energy_list(const EnergyListParams &p, int S, cudaStream_t s);
+struct EnergyList2 {
+    EnergyListParams set[2];
+};
+cudaError_t launch_energy_list(const EnergyList2 &p, int n_sets, int S, cudaStream_t s);
 
 // Metropolis-Hastings decision and state update of every proposal row.
 struct MHParams {
