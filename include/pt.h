@@ -235,6 +235,13 @@ int pt_set_global_every(pt_ctx *ctx, int every);
  * exact acceptance ratio (the kept modes' terms cancel).  Default {0, ..., 7}.  PT_EINVAL outside 0..7. */
 int pt_set_global_blocks(pt_ctx *ctx, int lo, int hi);
 
+/* How a move's autoregressive sampling runs: one_launch != 0 (the default) runs the network passes of all mode
+ * blocks and the draws in one launch with the network's weights held on chip, when the proposal rows per
+ * sample (n_cold x replicas) are at most 64; one_launch == 0 (or more rows) launches a network pass and a
+ * sampling kernel per block.  Both draw identical proposals (same random streams, same arithmetic).
+ * PT_EINVAL before pt_learn_init. */
+int pt_set_global_sampler(pt_ctx *ctx, int one_launch);
+
 /* FP32 master parameters of all samples, [S][psize] (layout from pt_learn_shape): set != 0 uploads them
  * (and refreshes the BF16 copies), set == 0 downloads them. */
 int pt_learn_params(pt_ctx *ctx, float *params, int set);

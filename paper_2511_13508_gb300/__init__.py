@@ -49,7 +49,7 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
            "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
-           "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_gemm_bf16",
+           "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_set_global_sampler", "pt_gemm_bf16",
            "pt_energy_fp64_static", "pt_fmc_graph", "pt_create_graph", "pt_check_wait"]
 
 _lib = None
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.pt_global_move.argtypes = [vp]
         L.pt_set_global_every.argtypes = [vp, i]
         L.pt_set_global_blocks.argtypes = [vp, i, i]
+        L.pt_set_global_sampler.argtypes = [vp, i]
         L.pt_learn_params.argtypes = [vp, vp, i]
         L.pt_learn_shape.argtypes = [vp, vp]
         L.pt_learn_eval.argtypes = [vp, vp, vp, i, vp, vp, vp]
@@ -318,6 +319,11 @@ class PT:
 
     def set_global_blocks(self, lo, hi):
         self._c(lib().pt_set_global_blocks(self._h, int(lo), int(hi)))
+
+    def set_global_sampler(self, one_launch=True):
+        """One-launch autoregressive sampling (default, <= 64 proposal rows per sample) or one launch per block;
+        both draw identical proposals."""
+        self._c(lib().pt_set_global_sampler(self._h, 1 if one_launch else 0))
 
     def running_energies(self):
         """Running FP64 energies of all chains, canonical (s, r, t) order (no recompute)."""

@@ -138,6 +138,7 @@ struct SegKey {
 struct LearnState {
     ptgb::LearnShape sh{};
     int Mb = 0, ncap = 0, ndata = 0, nprop = 0, rows = 0, global_every = 0, adam_t = 0;
+    bool one_launch = true;  // autoregressive sampling in one launch (nprop <= 64)
     int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
     uint64_t seed = 0;
@@ -375,23 +376,34 @@ template <typename T> T *lalloc(pt_ctx *c, size_t count, int *rc) {
     return p;
 }
 
+// Arguments of the single-launch network forward (one cluster of blocks per sample, outputs into L.O).
+MlpParams mlp_params(pt_ctx *c, const __nv_bfloat16 *X, int rows, const int *cond, int64_t strideCond) {
+    LearnState &L = *c->learn;
+    const ptgb::LearnShape &sh = L.sh;
+    const int64_t rc = L.rows;
+    MlpParams m{};
+    m.X = X; m.strideX = rc * sh.Din; m.ldx = sh.Din; m.M = rows; m.Din = sh.Din; m.H = sh.H; m.Dout = sh.Dout;
+    m.W1c = L.W1c; m.W2c = L.W2c; m.W3c = L.W3c;
+    m.strideW1 = (int64_t)sh.H * sh.Din; m.strideW2 = (int64_t)sh.H * sh.H; m.strideW3 = (int64_t)sh.Dout * sh.H;
+    m.P = L.P; m.psize = (int64_t)sh.psize; m.ob1 = sh.ob1; m.oC1 = sh.oC1; m.ob2 = sh.ob2; m.ob3 = sh.ob3;
+    m.cond = cond; m.strideCond = strideCond; m.ncond = sh.ncold;
+    m.O = L.O; m.strideO = rc * sh.Dout; m.ldo = sh.Dout;
+    m.err = &c->d_ctl->error;
+    return m;
+}
+
 // Dense layers on the tensor cores: O = W3 relu(W2 relu(W1 x + b1 + C1[cond]) + b2) + b3 for `rows` rows of
 // every sample; with `train` the transposed activations the weight gradients need are kept as well.
 int learn_forward(pt_ctx *c, const __nv_bfloat16 *X, int rows, const int *cond, int64_t strideCond, bool train) {
     LearnState &L = *c->learn;
     const ptgb::LearnShape &sh = L.sh;
     const int64_t rc = L.rows;
-    if (!train && rows <= 128) {  // sampling passes: the whole network in one launch, activations on chip
-        MlpParams m{};
-        m.X = X; m.strideX = rc * sh.Din; m.ldx = sh.Din; m.M = rows; m.Din = sh.Din; m.H = sh.H; m.Dout = sh.Dout;
-        m.W1c = L.W1c; m.W2c = L.W2c; m.W3c = L.W3c;
-        m.strideW1 = (int64_t)sh.H * sh.Din; m.strideW2 = (int64_t)sh.H * sh.H; m.strideW3 = (int64_t)sh.Dout * sh.H;
-        m.P = L.P; m.psize = (int64_t)sh.psize; m.ob1 = sh.ob1; m.oC1 = sh.oC1; m.ob2 = sh.ob2; m.ob3 = sh.ob3;
-        m.cond = cond; m.strideCond = strideCond;
-        m.O = L.O; m.strideO = rc * sh.Dout; m.ldo = sh.Dout;
-        m.err = &c->d_ctl->error;
-        CK(launch_fused_mlp(m, c->S, c->stream));
-        return PT_OK;
+    if (!train) {  // sampling passes: the whole network in one launch, activations on chip
+        const MlpParams m = mlp_params(c, X, rows, cond, strideCond);
+        if (fused_mlp_supported(m, false)) {
+            CK(launch_fused_mlp(m, c->S, c->stream));
+            return PT_OK;
+        }
     }
     GemmParams g{};
     g.A = X; g.strideA = rc * sh.Din; g.lda = sh.Din;
@@ -500,19 +512,27 @@ int run_global(pt_ctx *c) {
     CK(launch_density(dc, c->S, c->stream));
     // autoregressive sampling, one pass per block of modes from the first resampled block of each row on;
     // the blocks below it keep the current configuration's features and variables
-    CK(cudaMemcpyAsync(L.Xp, L.X, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din, cudaMemcpyDeviceToDevice,
-                       c->stream));
     CK(cudaMemcpyAsync(L.rsamp.u, L.rcur.u, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(L.rsamp.phi, L.rcur.phi, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice,
                        c->stream));
-    for (int b = L.blk_lo; b < ptgb::kLearnBlocks; ++b) {
-        if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
-        SampleParams sp{};
-        sp.O = L.O; sp.rows_per_sample = np; sp.N = sh.N; sp.Dout = sh.Dout; sp.Din = sh.Din; sp.block = b;
-        sp.lo = L.blk_lo; sp.hi = L.blk_hi;
-        sp.seed = c->seed; sp.row_id = L.prow; sp.ctl = c->d_ctl; sp.X = L.Xp; sp.u = L.rsamp.u; sp.phi = L.rsamp.phi;
-        sp.o_stride = L.rows; sp.x_stride = L.rows;
-        CK(launch_sample_block(sp, c->S, c->stream));
+    const MlpParams ms = mlp_params(c, L.X, np, L.pcond, np);
+    if (L.one_launch && fused_mlp_supported(ms, true)) {  // all passes in one launch, weights resident on chip
+        SamplerExtra sx{};
+        sx.seed = c->seed; sx.row_id = L.prow; sx.ctl = c->d_ctl; sx.lo = L.blk_lo; sx.hi = L.blk_hi; sx.N = sh.N;
+        sx.u = L.rsamp.u; sx.phi = L.rsamp.phi;
+        CK(launch_fused_sampler(ms, sx, c->S, c->stream));
+    } else {  // one network pass and one sampling launch per block
+        CK(cudaMemcpyAsync(L.Xp, L.X, sizeof(__nv_bfloat16) * (size_t)c->S * L.rows * sh.Din,
+                           cudaMemcpyDeviceToDevice, c->stream));
+        for (int b = L.blk_lo; b < ptgb::kLearnBlocks; ++b) {
+            if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
+            SampleParams sp{};
+            sp.O = L.O; sp.rows_per_sample = np; sp.N = sh.N; sp.Dout = sh.Dout; sp.Din = sh.Din; sp.block = b;
+            sp.lo = L.blk_lo; sp.hi = L.blk_hi;
+            sp.seed = c->seed; sp.row_id = L.prow; sp.ctl = c->d_ctl; sp.X = L.Xp; sp.u = L.rsamp.u;
+            sp.phi = L.rsamp.phi; sp.o_stride = L.rows; sp.x_stride = L.rows;
+            CK(launch_sample_block(sp, c->S, c->stream));
+        }
     }
     AssembleParams ap{};
     ap.u = L.rsamp.u; ap.phi = L.rsamp.phi; ap.rows_per_sample = np; ap.N = sh.N; ap.seed = c->seed;
@@ -1664,6 +1684,16 @@ int pt_set_global_blocks(pt_ctx *c, int lo, int hi) {
     c->learn->blk_lo = lo;
     c->learn->blk_hi = hi;
     drop_graphs(c);  // the range is baked into captured segments
+    return PT_OK;
+}
+
+int pt_set_global_sampler(pt_ctx *c, int one_launch) {
+    if (!c) return fail(nullptr, PT_EINVAL, "pt_set_global_sampler: NULL context");
+    if (!c->learn) return fail(c, PT_EINVAL, "pt_set_global_sampler: call pt_learn_init first");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    c->learn->one_launch = one_launch != 0;
+    drop_graphs(c);  // the choice is baked into captured segments
     return PT_OK;
 }
 

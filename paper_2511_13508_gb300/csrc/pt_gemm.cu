@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include "pt_common.cuh"
 #include "pt_gemm.h"
+#include "pt_learn.h"
+#include "pt_learn_dev.cuh"
 
 namespace ptgb {
 
@@ -308,6 +310,16 @@ __device__ __forceinline__ void st_cluster16(uint32_t local, uint32_t rank, uint
                  : "memory");
 }
 
+// 2 bytes to the same shared-memory offset in block `rank` of the cluster
+__device__ __forceinline__ void st_cluster2(uint32_t local, uint32_t rank, uint16_t v) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(remote), "h"(v) : "memory");
+}
+
+constexpr size_t kMlpSmemMax = 227 * 1024 - 2048;  // dynamic shared memory of a cluster block (static part aside)
+constexpr int kMlpMaxCond = 64;                     // conditions whose C1 columns are staged in shared memory
+
 // One layer's products: TMEM[0..NS) = act (128 x K) * Wslice^T, issued by one thread, completion on `done`.
 __device__ __forceinline__ void mlp_mma(uint32_t tmem, uint32_t abuf, uint32_t lboA, uint32_t wbuf, int NS, int K,
                                        uint64_t *done) {
@@ -328,7 +340,13 @@ __device__ __forceinline__ void mlp_mma(uint32_t tmem, uint32_t abuf, uint32_t l
 
 }  // namespace
 
-__global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1) fused_mlp_kernel(MlpParams p) {
+// With kSampler the block also runs the autoregressive sampling of the learned proposal (see SamplerParams):
+// one pass of the network per mode block b = lo..7 with the weights resident in shared memory; after pass b
+// the block holding block b's outputs draws its modes for the rows that resample it, writes the draws to
+// global memory and their input features into the input buffer of every block of the cluster.
+template <bool kSampler>
+__global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
+    mlp_cluster_kernel(MlpParams p, SamplerExtra sx) {
     extern __shared__ __align__(1024) unsigned char msm[];
     __shared__ uint64_t full[3], done;
     __shared__ uint32_t tmem_base_slot;
@@ -339,9 +357,18 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     const int Mp = (p.M + 15) & ~15;
     const uint32_t lboA = (uint32_t)Mp * 16u;
     const uint32_t act_bytes = 32u * lboA + kMlpPad;  // 256 K columns
-    const uint32_t sAct0 = smem_addr(msm), sAct1 = sAct0 + act_bytes;
+    const uint32_t x_bytes = kSampler ? (uint32_t)(p.Din / 8) * lboA + kMlpPad : 0u;
+    // H2 | H1 | [X] | W1 | W2 | W3 slices; without the sampler the input shares the H2 buffer
+    const uint32_t sH2 = smem_addr(msm), sH1 = sH2 + act_bytes, sX = kSampler ? sH1 + act_bytes : sH2;
     const uint32_t wbytes[3] = {(uint32_t)p.Din * NS * 2u, (uint32_t)p.H * NS * 2u, (uint32_t)p.H * NS3 * 2u};
-    const uint32_t sW[3] = {sAct1 + act_bytes, sAct1 + act_bytes + wbytes[0], sAct1 + act_bytes + wbytes[0] + wbytes[1]};
+    const uint32_t w0 = sH1 + act_bytes + x_bytes;
+    const uint32_t sW[3] = {w0, w0 + wbytes[0], w0 + wbytes[0] + wbytes[1]};
+    // after the weights: C1's columns of this block (if staged), then (sampler) the outputs of a mode block
+    // [Mp][32] and the first resampled block of each row
+    const bool stage_c1 = p.ncond <= kMlpMaxCond;
+    float *c1s = reinterpret_cast<float *>(msm + (w0 - sH2) + wbytes[0] + wbytes[1] + wbytes[2]);
+    float *obuf = c1s + (stage_c1 ? p.ncond * NS : 0);
+    int *fbs = reinterpret_cast<int *>(obuf + (kSampler ? Mp * 32 : 0));
     const unsigned char *gW[3] = {
         reinterpret_cast<const unsigned char *>(p.W1c + (int64_t)b * p.strideW1) + (size_t)rank * wbytes[0],
         reinterpret_cast<const unsigned char *>(p.W2c + (int64_t)b * p.strideW2) + (size_t)rank * wbytes[1],
@@ -369,7 +396,14 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
         bsl[1][threadIdx.x] = P[p.ob2 + rank * NS + threadIdx.x];
         bsl[2][threadIdx.x] = threadIdx.x < NS3 ? P[p.ob3 + rank * NS3 + threadIdx.x] : 0.f;
     }
-    stage_rows(sAct0, p.X + (int64_t)b * p.strideX, p.ldx, Mp, p.M, 0, p.Din / 8, lboA);
+    if (kSampler)
+        for (int rw = threadIdx.x; rw < p.M; rw += blockDim.x)
+            fbs[rw] = first_block(sx.seed, sx.row_id[(int64_t)b * p.M + rw], (uint32_t)sx.ctl->global_rounds, sx.N,
+                                  sx.lo, sx.hi);
+    if (stage_c1)  // this block's columns of C1, all conditions
+        for (int i = threadIdx.x; i < p.ncond * NS; i += blockDim.x)
+            c1s[i] = P[p.oC1 + (int64_t)(i / NS) * p.H + rank * NS + i % NS];
+    stage_rows(sX, p.X + (int64_t)b * p.strideX, p.ldx, Mp, p.M, 0, p.Din / 8, lboA);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     cluster_arrive();  // this block runs: the others may write into its shared memory once they have waited
@@ -379,67 +413,123 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     const uint32_t tmem = tmem_base_slot;
     const int *cond = p.cond + (int64_t)b * p.strideCond;
     const int quad = warp % 4, part = warp / 4, row = quad * 32 + lane;
+    // sampler: the draws' round and each proposal row's first resampled block
+    const uint32_t round = kSampler ? (uint32_t)sx.ctl->global_rounds : 0u;
     bool ok = true;
-    for (int l = 0; l < 3; ++l) {
-        const int nsl = l < 2 ? NS : NS3;
-        if (threadIdx.x == 0) {
-            if (mbar_wait(&full[l], 0u)) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                mlp_mma(tmem, l == 1 ? sAct1 : sAct0, lboA, sW[l], nsl, l == 0 ? p.Din : p.H, &done);
-            } else {
-                ok = false;
-            }
-        }
-        __syncwarp();
-        if (!mbar_wait(&done, (uint32_t)l & 1u)) ok = false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // every block takes part in every cluster barrier, whatever its status, so that none waits forever
-        const int span = nsl / 2, c0 = part * span, ncol = min(32, span);
-        uint32_t r[32];
-        if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-        if (l < 2) {
-            if (l == 0) cluster_wait();  // all blocks of the cluster have started
-            if (quad * 32 < Mp && row < Mp && ok) {
-                const bool live = row < p.M;
-                const float *cb = (l == 0 && live) ? P + p.oC1 + (int64_t)cond[row] * p.H + rank * NS + c0 : nullptr;
-                float cv[32];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) cv[q] = (cb && q < ncol) ? cb[q] : 0.f;
-                const uint32_t dst = (l == 0 ? sAct1 : sAct0) + (uint32_t)row * 16u;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    if (8 * g >= ncol) break;
-                    uint32_t w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int q = 8 * g + 2 * e;
-                        float v0 = __uint_as_float(r[q]) + bsl[l][c0 + q] + cv[q];
-                        float v1 = __uint_as_float(r[q + 1]) + bsl[l][c0 + q + 1] + cv[q + 1];
-                        v0 = live ? fmaxf(v0, 0.f) : 0.f;
-                        v1 = live ? fmaxf(v1, 0.f) : 0.f;
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                        w[e] = *reinterpret_cast<const uint32_t *>(&h);
-                    }
-                    const uint32_t kg = (uint32_t)(rank * NS + c0 + 8 * g) / 8;
-                    const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
-                    for (uint32_t dstr = 0; dstr < (uint32_t)kMlpCL; ++dstr) st_cluster16(dst + kg * lboA, dstr, v);
+    uint32_t n_commits = 0;
+    const int pass0 = kSampler ? sx.lo : 0, pass1 = kSampler ? kLearnBlocks : 1;
+    bool first_wait = true;
+    for (int pass = pass0; pass < pass1; ++pass) {
+        for (int l = 0; l < 3; ++l) {
+            const int nsl = l < 2 ? NS : NS3;
+            if (threadIdx.x == 0) {
+                if (!first_wait || mbar_wait(&full[l], 0u)) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    mlp_mma(tmem, l == 0 ? sX : (l == 1 ? sH1 : sH2), lboA, sW[l], nsl, l == 0 ? p.Din : p.H, &done);
+                } else {
+                    ok = false;
                 }
             }
-            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");  // generic writes -> tensor core reads
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            cluster_arrive();
-            cluster_wait();
+            __syncwarp();
+            if (!mbar_wait(&done, n_commits & 1u)) ok = false;
+            ++n_commits;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        } else if (quad * 32 < Mp && row < p.M && ok) {
-            float *o = p.O + (int64_t)b * p.strideO + (int64_t)row * p.ldo + rank * NS3 + c0;
+            // every block takes part in every cluster barrier, whatever its status, so that none waits forever
+            const int span = nsl / 2, c0 = part * span, ncol = min(32, span);
+            uint32_t r[32];
+            if (l < 2) {
+                if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
+                if (first_wait && l == 0) cluster_wait();  // all blocks of the cluster have started
+                if (quad * 32 < Mp && row < Mp && ok) {
+                    const bool live = row < p.M;
+                    const float *cb = (l == 0 && live) ? (stage_c1 ? c1s + cond[row] * NS + c0
+                                                                   : P + p.oC1 + (int64_t)cond[row] * p.H + rank * NS + c0)
+                                                       : nullptr;
+                    float cv[32];
 #pragma unroll
-            for (int q = 0; q < 32; q += 4)
-                if (q < ncol)
-                    *reinterpret_cast<float4 *>(o + q) =
-                        make_float4(__uint_as_float(r[q]) + bsl[2][c0 + q], __uint_as_float(r[q + 1]) + bsl[2][c0 + q + 1],
-                                    __uint_as_float(r[q + 2]) + bsl[2][c0 + q + 2],
-                                    __uint_as_float(r[q + 3]) + bsl[2][c0 + q + 3]);
+                    for (int q = 0; q < 32; ++q) cv[q] = (cb && q < ncol) ? cb[q] : 0.f;
+                    const uint32_t dst = (l == 0 ? sH1 : sH2) + (uint32_t)row * 16u;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if (8 * g >= ncol) break;
+                        uint32_t w[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 8 * g + 2 * e;
+                            float v0 = __uint_as_float(r[q]) + bsl[l][c0 + q] + cv[q];
+                            float v1 = __uint_as_float(r[q + 1]) + bsl[l][c0 + q + 1] + cv[q + 1];
+                            v0 = live ? fmaxf(v0, 0.f) : 0.f;
+                            v1 = live ? fmaxf(v1, 0.f) : 0.f;
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                            w[e] = *reinterpret_cast<const uint32_t *>(&h);
+                        }
+                        const uint32_t kg = (uint32_t)(rank * NS + c0 + 8 * g) / 8;
+                        const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
+                        for (uint32_t dstr = 0; dstr < (uint32_t)kMlpCL; ++dstr) st_cluster16(dst + kg * lboA, dstr, v);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");  // generic writes -> tensor core reads
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                cluster_arrive();
+                cluster_wait();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            } else if (!kSampler) {
+                if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
+                if (quad * 32 < Mp && row < p.M && ok) {
+                    float *o = p.O + (int64_t)b * p.strideO + (int64_t)row * p.ldo + rank * NS3 + c0;
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4)
+                        if (q < ncol)
+                            *reinterpret_cast<float4 *>(o + q) = make_float4(
+                                __uint_as_float(r[q]) + bsl[2][c0 + q], __uint_as_float(r[q + 1]) + bsl[2][c0 + q + 1],
+                                __uint_as_float(r[q + 2]) + bsl[2][c0 + q + 2],
+                                __uint_as_float(r[q + 3]) + bsl[2][c0 + q + 3]);
+                }
+            } else {
+                // mode block `pass`: modes [pass per, (pass+1) per), output columns 4 per wide, held by block
+                // rank pass / 2, warp part pass % 2 (each block's slice covers two mode blocks).  The owning warps
+                // park the outputs (+ b3) in shared memory; then all threads of that block draw one (row, mode)
+                // pair each.
+                const int per = sx.N / kLearnBlocks;
+                if ((int)rank == pass / 2) {
+                    if (part == pass % 2 && quad * 32 < Mp) {
+                        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
+                        if (row < Mp)
+#pragma unroll
+                            for (int q = 0; q < 32; ++q)
+                                if (q < 4 * per) obuf[row * 32 + q] = __uint_as_float(r[q]) + bsl[2][c0 + q];
+                    }
+                    __syncthreads();
+                    for (int idx = threadIdx.x; idx < p.M * per && ok; idx += blockDim.x) {
+                        const int rw = idx / per, t = idx % per, k = pass * per + t;
+                        if (pass < fbs[rw]) continue;
+                        const int64_t gr = (int64_t)b * p.M + rw;
+                        const float o[4] = {obuf[rw * 32 + 4 * t], obuf[rw * 32 + 4 * t + 1], obuf[rw * 32 + 4 * t + 2],
+                                            obuf[rw * 32 + 4 * t + 3]};
+                        const u32x4 w = draw(sx.seed, sx.row_id[gr], round, (uint32_t)k, kTagGlobal);
+                        float u, ph;
+                        sample_mode(o, w, k, sx.N, &u, &ph);
+                        sx.u[gr * sx.N + k] = u;
+                        sx.phi[gr * sx.N + k] = ph;
+                        float f[3];
+                        feature_triplet(u, ph, k, sx.N, f);
+                        for (int c = 0; c < 3; ++c) {
+                            const uint32_t fi = (uint32_t)(3 * k + c);
+                            const __nv_bfloat16 h = __float2bfloat16_rn(f[c]);
+                            const uint16_t bits = *reinterpret_cast<const uint16_t *>(&h);
+                            const uint32_t off = sX + (fi / 8) * lboA + (uint32_t)rw * 16u + (fi % 8) * 2u;
+                            for (uint32_t dstr = 0; dstr < (uint32_t)kMlpCL; ++dstr) st_cluster2(off, dstr, bits);
+                        }
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                cluster_arrive();
+                cluster_wait();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
         }
+        first_wait = false;
     }
     if (!ok && threadIdx.x == 0) {
         if (p.err) atomicCAS(p.err, 0, kErrTimeout);
@@ -451,28 +541,53 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
-cudaError_t launch_fused_mlp(const MlpParams &p, int batch, cudaStream_t s) {
-    // M <= 128 rows; Din a multiple of 16 (<= 192); H = 256; Dout/4 a multiple of 16 (<= 64); 16-byte aligned
-    // weights; O rows 16-byte aligned
-    if (p.M < 1 || p.M > 128 || p.Din < 16 || p.Din > 192 || (p.Din % 16) || p.H != 256 || p.Dout < 64 ||
-        p.Dout > 256 || (p.Dout % 64) || (p.ldo % 4) || batch < 1 || !p.W1c || !p.W2c || !p.W3c ||
-        ((uintptr_t)p.W1c | (uintptr_t)p.W2c | (uintptr_t)p.W3c) % 16 ||
-        ((p.strideW1 | p.strideW2 | p.strideW3) * 2) % 16)
-        return cudaErrorInvalidValue;
-    const int Mp = (p.M + 15) & ~15;
-    const size_t act = 2 * (32 * (size_t)Mp * 16 + kMlpPad);
+namespace {
+
+// Shared memory of a cluster block, or 0 if the shapes are outside what the kernel handles.
+size_t mlp_cluster_smem(const MlpParams &p, bool sampler) {
+    // M <= 128 rows (<= 64 with the sampler); Din a multiple of 16 (<= 192); H = 256; Dout/4 a multiple of 16
+    // (<= 64); 16-byte aligned weights; O rows 16-byte aligned
+    if (p.M < 1 || p.M > (sampler ? 64 : 128) || p.ncond < 1 || p.Din < 16 || p.Din > 192 || (p.Din % 16) || p.H != 256 ||
+        p.Dout < 64 || p.Dout > 256 || (p.Dout % 64) || (p.ldo % 4) || !p.W1c || !p.W2c || !p.W3c ||
+        ((uintptr_t)p.W1c | (uintptr_t)p.W2c | (uintptr_t)p.W3c) % 16 || ((p.strideW1 | p.strideW2 | p.strideW3) * 2) % 16)
+        return 0;
+    const size_t Mp = (size_t)((p.M + 15) & ~15);
+    size_t act = 2 * (32 * Mp * 16 + kMlpPad);
+    if (sampler) act += (size_t)(p.Din / 8) * Mp * 16 + kMlpPad;
     const size_t w = ((size_t)p.Din + p.H) * (p.H / kMlpCL) * 2 + (size_t)p.H * (p.Dout / kMlpCL) * 2;
-    const size_t sm = act + w;
-    constexpr size_t kSmemMax = 227 * 1024 - 2048;  // minus the static part
-    if (sm > kSmemMax) return cudaErrorInvalidValue;
+    size_t extra = p.ncond <= kMlpMaxCond ? (size_t)p.ncond * (p.H / kMlpCL) * 4 : 0;
+    if (sampler) extra += Mp * 32 * 4 + (size_t)p.M * 4;
+    return act + w + extra <= kMlpSmemMax ? act + w + extra : 0;
+}
+
+template <bool kSampler>
+cudaError_t launch_mlp_cluster(const MlpParams &p, const SamplerExtra &sx, int batch, cudaStream_t s) {
+    const size_t sm = mlp_cluster_smem(p, kSampler);
+    if (sm == 0 || batch < 1) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fused_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        cudaError_t e = cudaFuncSetAttribute(mlp_cluster_kernel<kSampler>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMlpSmemMax);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    fused_mlp_kernel<<<batch * kMlpCL, kMlpThreads, sm, s>>>(p);
+    mlp_cluster_kernel<kSampler><<<batch * kMlpCL, kMlpThreads, sm, s>>>(p, sx);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_mlp_supported(const MlpParams &p, bool sampler) { return mlp_cluster_smem(p, sampler) != 0; }
+
+cudaError_t launch_fused_mlp(const MlpParams &p, int batch, cudaStream_t s) {
+    return launch_mlp_cluster<false>(p, SamplerExtra{}, batch, s);
+}
+
+cudaError_t launch_fused_sampler(const MlpParams &p, const SamplerExtra &sx, int batch, cudaStream_t s) {
+    if (sx.N < kLearnBlocks || sx.N % kLearnBlocks || sx.N * 4 != p.Dout || sx.lo < 0 || sx.lo > sx.hi ||
+        sx.hi >= kLearnBlocks || !sx.row_id || !sx.ctl || !sx.u || !sx.phi)
+        return cudaErrorInvalidValue;
+    return launch_mlp_cluster<true>(p, sx, batch, s);
 }
 
 cudaError_t launch_gemm_bf16(const GemmParams &p, int batch, cudaStream_t s) {

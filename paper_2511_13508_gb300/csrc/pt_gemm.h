@@ -54,13 +54,31 @@ struct MlpParams {
     const float *P;          // FP32 master parameters [batch][psize]: biases b1, C1, b2, b3
     int64_t psize;
     int64_t ob1, oC1, ob2, ob3;
-    const int *cond;         // [batch][strideCond] temperature index per row
+    const int *cond;         // [batch][strideCond] temperature index per row, in [0, ncond)
     int64_t strideCond;
+    int ncond;               // rows of C1
     float *O;                // [batch][strideO], rows of ldo
     int64_t strideO;
     int ldo;
     int *err;
 };
 cudaError_t launch_fused_mlp(const MlpParams &p, int batch, cudaStream_t s);
+// Whether the single-launch forward (sampler = false) or the one-launch sampler (true) takes these shapes.
+bool fused_mlp_supported(const MlpParams &p, bool sampler);
+
+struct Control;
+// The autoregressive sampling of the learned proposal in one launch (network weights resident on chip): for
+// mode blocks b = lo..7 a pass of the network over the input features X (the current configurations'
+// features on entry; M = proposal rows per sample <= 64), then the draws of block b's modes for the rows whose
+// first resampled block is <= b, written to u, phi ([batch][M][N]) and, as input features, into the next pass.
+// The draws are those of the block-wise sampling kernel (same Philox streams, same arithmetic).
+struct SamplerExtra {
+    uint64_t seed;
+    const uint32_t *row_id;  // [batch][M] chain ids (stream of the draws)
+    const Control *ctl;      // global_rounds = round of the draws
+    int lo, hi, N;           // range of the first resampled block; modes
+    float *u, *phi;
+};
+cudaError_t launch_fused_sampler(const MlpParams &p, const SamplerExtra &sx, int batch, cudaStream_t s);
 
 }  // namespace ptgb

@@ -7,29 +7,11 @@
 #include <cuda_bf16.h>
 #include "pt_common.cuh"
 #include "pt_learn.h"
+#include "pt_learn_dev.cuh"
 
 namespace ptgb {
 
 namespace {
-
-constexpr float kTwoPiF = 6.28318530717958647692f;
-constexpr float kLog2PiHalf = 0.91893853320467274178f;  // log(2 pi) / 2
-constexpr float kRhoMax = 0.98f;
-constexpr float kUScale = 0.25f;                          // input scale of logit(v)
-
-// uniform in (0, 1) from the top 24 bits of a Philox word (FP32 draws)
-__device__ __forceinline__ float u01f(uint32_t w) { return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f); }
-__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
-__device__ __forceinline__ float wrap2pi(float x) { return x - kTwoPiF * floorf(x / kTwoPiF); }
-
-// Input features of mode k: (logit(v_k)/4 clipped to [-4, 4], cos phi~_k, sin phi~_k).
-__device__ __forceinline__ void feature_triplet(float u, float ph, int k, int N, float f[3]) {
-    f[0] = (k <= N - 2) ? fminf(fmaxf(u * kUScale, -4.f), 4.f) : 0.f;
-    float sn, cs;
-    sincosf(ph, &sn, &cs);
-    f[1] = cs;
-    f[2] = sn;
-}
 
 __device__ __forceinline__ double warp_sumd(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -333,17 +315,9 @@ __global__ void sample_block_kernel(SampleParams p) {
         const int k = p.block * per + t;
         const float *o = p.O + ((int64_t)s * p.o_stride + row) * p.Dout + 4 * k;
         const u32x4 w = draw(p.seed, id, (uint32_t)p.ctl->global_rounds, (uint32_t)k, kTagGlobal);
-        float u = 0.f, ph = 0.f;
-        if (k <= N - 2) {
-            const float ls = fminf(fmaxf(o[1], -7.f), 3.f);
-            const float eps = sqrtf(-2.f * logf(u01f(w.x))) * cosf(kTwoPiF * u01f(w.y));  // Box-Muller
-            u = o[0] + expf(ls) * eps;
-        }
-        if (k >= 2) {
-            const float rho = kRhoMax / (1.f + expf(-o[3]));
-            const float t1 = tanf(3.14159265358979323846f * (u01f(w.z) - 0.5f));
-            ph = wrap2pi(o[2] + 2.f * atanf((1.f - rho) / (1.f + rho) * t1));
-        }
+        const float ov[4] = {o[0], o[1], o[2], o[3]};
+        float u, ph;
+        sample_mode(ov, w, k, N, &u, &ph);
         p.u[grow * N + k] = u;
         p.phi[grow * N + k] = ph;
         float f[3];

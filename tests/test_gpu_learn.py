@@ -339,6 +339,36 @@ def test_accepted_global_moves_carry_the_energy_of_the_stored_state(prec):
         assert abs(E[c] - ref) <= 1e-13 * np.abs(J[s_]).sum(), (c, E[c], ref)
 
 
+@pytest.mark.parametrize("N,R,ncold,blocks", [(64, 4, 4, (0, 7)), (32, 8, 3, (2, 6)), (16, 16, 4, (0, 0))])
+def test_one_launch_sampler_draws_the_per_block_proposals(N, R, ncold, blocks):
+    """The autoregressive sampling in one launch (network weights on chip, draws written into the next pass's
+    input in distributed shared memory) must draw exactly the proposals of the per-block launches: the same
+    random streams and arithmetic, so after a series of global moves both ensembles hold bit-identical states,
+    energies and acceptance counts."""
+    S, nT = 2, 4
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    J = [0.05 * j for j in _couplings([N] * S)]
+    runs = []
+    for one in (True, False):
+        pt = pkg.PT([N] * S, J, temps, R, 77, precision="fp32")
+        pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
+        sh = pt.learn_shape()
+        rng = np.random.default_rng(5)
+        P = _randomise_outputs(pt.learn_params().astype(np.float64), sh, rng, scale=0.3)
+        pt.set_learn_params(_stick_breaking_biases(N, P, sh).astype(np.float32))
+        pt.set_global_blocks(*blocks)
+        pt.set_global_sampler(one)
+        for _ in range(6):
+            pt.global_move()
+        a, E = pt.state()
+        o = pt.observables()
+        runs.append((a, E, o["gm_acc"].copy(), o["gm_att"].copy()))
+        pt.close()
+    (a1, E1, acc1, att1), (a2, E2, acc2, att2) = runs
+    assert acc1.sum() > 0 and np.array_equal(att1, att2)
+    assert np.array_equal(acc1, acc2) and np.array_equal(a1, a2) and np.array_equal(E1, E2)
+
+
 def test_training_lowers_the_nll_and_raises_acceptance():
     N, S, R, nT, ncold = 16, 4, 16, 8, 4
     temps = workload.geometric_ladder(0.4, 1.6, nT)
