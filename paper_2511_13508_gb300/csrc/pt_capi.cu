@@ -139,6 +139,9 @@ struct LearnState {
     ptgb::LearnShape sh{};
     int Mb = 0, ncap = 0, ndata = 0, nprop = 0, rows = 0, global_every = 0, adam_t = 0;
     bool one_launch = true;  // autoregressive sampling in one launch (nprop <= 64)
+    cudaStream_t side = nullptr;  // the current configurations' density and energy, concurrent with the sampling
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    float *Ocur = nullptr;        // network outputs of the current configurations [S][nprop][Dout]
     int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
     uint64_t seed = 0;
@@ -485,9 +488,9 @@ int learn_cast(pt_ctx *c) {
     return PT_OK;
 }
 
-DensityParams density_params(LearnState &L, const RawRows &raw, double *logq, int rows, bool grad) {
+DensityParams density_params(LearnState &L, const float *O, const RawRows &raw, double *logq, int rows, bool grad) {
     DensityParams d{};
-    d.O = L.O; d.raw = raw; d.rows_per_sample = rows; d.N = L.sh.N; d.Dout = L.sh.Dout; d.logq = logq;
+    d.O = O; d.raw = raw; d.rows_per_sample = rows; d.N = L.sh.N; d.Dout = L.sh.Dout; d.logq = logq;
     d.inv_rows = 1.0f / (float)rows;
     d.o_stride = L.rows;
     if (grad) { d.dO = L.dO; d.dOb = L.dOb; d.dOT = L.dOT; d.lddt = L.rows; }
@@ -495,21 +498,43 @@ DensityParams density_params(LearnState &L, const RawRows &raw, double *logq, in
 }
 
 // One round of learned global moves on the chains at the ncold coldest temperatures of every sample.
+// When the network's forward pass fits one launch, the current configurations' density and energy run on a
+// second stream, concurrently with the sampling of the proposals (they share only the features X, which
+// neither side writes after the fork); the Metropolis-Hastings step waits for both.
 int run_global(pt_ctx *c) {
     LearnState &L = *c->learn;
     const ptgb::LearnShape &sh = L.sh;
     const int np = L.nprop;
     int rc;
     CK(launch_cold_rows(c->d_perm, c->S, c->R, c->nT, sh.ncold, L.pslot, L.prow, L.pcond, c->stream));
-    // current configurations: features, density, exact FP64 energy
+    // current configurations: features, then density and exact FP64 energy
     FeatParams fp{};
     fp.a = c->d_a; fp.dbl = c->dbl ? 1 : 0; fp.samples = c->d_samples; fp.slot = L.pslot; fp.rows_per_sample = np;
     fp.N = sh.N; fp.Din = sh.Din; fp.X = L.X; fp.XT = nullptr; fp.ldxt = L.rows; fp.raw = L.rcur;
     fp.raw_stride = np; fp.raw_off = 0; fp.cond_in = nullptr; fp.x_stride = L.rows;
     CK(launch_features(fp, c->S, c->stream));
-    if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
-    DensityParams dc = density_params(L, L.rcur, L.lq_cur, np, false);
-    CK(launch_density(dc, c->S, c->stream));
+    EnergyList2 el{};
+    EnergyListParams &ep = el.set[0];
+    ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
+    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
+    MlpParams mc = mlp_params(c, L.X, np, L.pcond, np);
+    mc.O = L.Ocur;
+    const bool split = fused_mlp_supported(mc, false);
+    if (split) {
+        CK(cudaEventRecord(L.ev_fork, c->stream));
+        CK(cudaStreamWaitEvent(L.side, L.ev_fork, 0));
+        CK(launch_fused_mlp(mc, c->S, L.side));
+        DensityParams dc = density_params(L, L.Ocur, L.rcur, L.lq_cur, np, false);
+        CK(launch_density(dc, c->S, L.side));
+        EnergyList2 e1{};
+        e1.set[0] = ep;
+        CK(launch_energy_list(e1, 1, c->S, L.side));
+        CK(cudaEventRecord(L.ev_join, L.side));
+    } else {
+        if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
+        DensityParams dc = density_params(L, L.O, L.rcur, L.lq_cur, np, false);
+        CK(launch_density(dc, c->S, c->stream));
+    }
     // autoregressive sampling, one pass per block of modes from the first resampled block of each row on;
     // the blocks below it keep the current configuration's features and variables
     CK(cudaMemcpyAsync(L.rsamp.u, L.rcur.u, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice, c->stream));
@@ -540,22 +565,24 @@ int run_global(pt_ctx *c) {
     ap.row_id = L.prow; ap.ctl = c->d_ctl; ap.a = L.a_prop;
     ap.a_cur = c->d_a; ap.dbl = c->dbl ? 1 : 0; ap.samples = c->d_samples; ap.slot = L.pslot;
     CK(launch_assemble(ap, c->S, c->stream));
-    // proposed configurations as stored: features, density, energy
+    // proposed configurations as stored: features (into Xp: the side stream may still read X), density, energy
     FeatParams fq = fp;
-    fq.a = L.a_prop; fq.dbl = 1; fq.slot = nullptr; fq.raw = L.rprop;
+    fq.a = L.a_prop; fq.dbl = 1; fq.slot = nullptr; fq.raw = L.rprop; fq.X = L.Xp;
     CK(launch_features(fq, c->S, c->stream));
-    if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
-    DensityParams dq = density_params(L, L.rprop, L.lq_prop, np, false);
+    if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
+    DensityParams dq = density_params(L, L.O, L.rprop, L.lq_prop, np, false);
     CK(launch_density(dq, c->S, c->stream));
-    // exact FP64 energies of the current configurations and of the proposals, one launch
-    EnergyList2 el{};
-    EnergyListParams &ep = el.set[0];
-    ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
-    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
     EnergyListParams &eq = el.set[1];
     eq = ep;
     eq.a = L.a_prop; eq.dbl = 1; eq.slot = nullptr; eq.E = L.H_prop;
-    CK(launch_energy_list(el, 2, c->S, c->stream));
+    if (split) {
+        EnergyList2 e2{};
+        e2.set[0] = eq;
+        CK(launch_energy_list(e2, 1, c->S, c->stream));
+        CK(cudaStreamWaitEvent(c->stream, L.ev_join, 0));
+    } else {
+        CK(launch_energy_list(el, 2, c->S, c->stream));  // both sets in one launch
+    }
     MHParams mp{};
     mp.logq_cur = L.lq_cur; mp.logq_prop = L.lq_prop; mp.H_cur = L.H_cur; mp.H_prop = L.H_prop;
     mp.extra_cur = L.rcur.extra; mp.extra_prop = L.rprop.extra; mp.a_prop = L.a_prop; mp.a = c->d_a;
@@ -1485,6 +1512,13 @@ int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_
     L->pslot = lalloc<int>(c, S * L->nprop, &rc); L->pcond = lalloc<int>(c, S * L->nprop, &rc);
     L->prow = lalloc<uint32_t>(c, S * L->nprop, &rc);
     L->a_prop = lalloc<double2>(c, S * L->nprop * N, &rc);
+    L->Ocur = lalloc<float>(c, S * L->nprop * sh.Dout, &rc);
+    if (rc == PT_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pt_learn_init: stream");
+    }
     L->max_losses = 1 << 16;
     L->losses = lalloc<double>(c, (size_t)L->max_losses, &rc);
     if (rc != PT_OK) return rc;
@@ -1584,7 +1618,7 @@ int pt_learn_eval(pt_ctx *c, const double *a, const int *cond, int rows, double 
     if (e == cudaSuccess) {
         rc = learn_forward(c, L.X, rows, L.raw.cond, rows, grad != nullptr);
         if (rc == PT_OK) {
-            DensityParams d = density_params(L, L.raw, L.logq, rows, grad != nullptr);
+            DensityParams d = density_params(L, L.O, L.raw, L.logq, rows, grad != nullptr);
             e = launch_density(d, c->S, c->stream);
             if (e == cudaSuccess && grad) rc = learn_backward(c, rows, L.raw.cond);
         }
@@ -1641,7 +1675,7 @@ int pt_train(pt_ctx *c, int steps, double lr, double *losses) {
         gp.X = L.X; gp.XT = L.XT; gp.raw = L.raw; gp.x_stride = L.rows;
         CK(launch_gather(gp, c->S, c->stream));
         if ((rc = learn_forward(c, L.X, L.Mb, L.raw.cond, L.Mb, true)) != PT_OK) return rc;
-        DensityParams d = density_params(L, L.raw, L.logq, L.Mb, true);
+        DensityParams d = density_params(L, L.O, L.raw, L.logq, L.Mb, true);
         CK(launch_density(d, c->S, c->stream));
         if ((rc = learn_backward(c, L.Mb, L.raw.cond)) != PT_OK) return rc;
         CK(launch_adam(L.P, L.Gr, L.Am, L.Av, (size_t)c->S * sh.psize, (float)lr, 0.9f, 0.999f, 1e-8f, ++L.adam_t,
@@ -1725,6 +1759,13 @@ int pt_sync(pt_ctx *c) {
 int pt_destroy(pt_ctx *c) {
     if (!c) return PT_OK;
     cudaStreamSynchronize(c->stream);
+    if (c->learn) {
+        if (c->learn->side) { cudaStreamSynchronize(c->learn->side); cudaStreamDestroy(c->learn->side); }
+        if (c->learn->ev_fork) cudaEventDestroy(c->learn->ev_fork);
+        if (c->learn->ev_join) cudaEventDestroy(c->learn->ev_join);
+        delete c->learn;
+        c->learn = nullptr;
+    }
     free_all(c);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
