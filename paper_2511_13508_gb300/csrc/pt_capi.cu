@@ -141,7 +141,7 @@ struct LearnState {
     bool one_launch = true;  // autoregressive sampling in one launch (nprop <= 64)
     cudaStream_t side = nullptr;  // the current configurations' density and energy, concurrent with the sampling
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    float *Ocur = nullptr;        // network outputs of the current configurations [S][nprop][Dout]
+    float *Ocur = nullptr;        // network outputs of the current configurations, laid out as O [S][rows][Dout]
     int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
     uint64_t seed = 0;
@@ -1512,7 +1512,7 @@ int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_
     L->pslot = lalloc<int>(c, S * L->nprop, &rc); L->pcond = lalloc<int>(c, S * L->nprop, &rc);
     L->prow = lalloc<uint32_t>(c, S * L->nprop, &rc);
     L->a_prop = lalloc<double2>(c, S * L->nprop * N, &rc);
-    L->Ocur = lalloc<float>(c, S * L->nprop * sh.Dout, &rc);
+    L->Ocur = lalloc<float>(c, S * rows * sh.Dout, &rc);  // the strides of O
     if (rc == PT_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming);
