@@ -392,6 +392,28 @@ def profile_case():
     return 0
 
 
+def profile_global():
+    """Eight learned global-move rounds on the learned-proposal workload (N=64, 16 samples x 32 T x 2 replicas,
+    8 coldest temperatures, a round every 8 sweeps; untrained network): 64 sweeps.  For the launch list of a
+    round."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    pkg.build()
+    W = workload.workloads()["n64_learned"]
+    nq = len(pkg.enumerate_quads(W.Ns[0]))
+    Js = [workload.couplings(W.Ns[0], nq, s) for s in W.seeds]
+    pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 4401, precision="fp32", stream=torch.cuda.Stream(),
+                swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
+    pt.learn_init(n_cold=W.extra["n_cold"], batch=512, data_per_sample=W.extra["train_configs"], seed=1)
+    pt.set_global_every(W.extra["global_every"])
+    pt.sweep(64)
+    pt.sync()
+    pt.close()
+    print("profile global done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,9 +426,13 @@ def main():
     ap.add_argument("--no-ladder", action="store_true", help="skip the adaptive-ladder leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
+    ap.add_argument("--profile-global", action="store_true",
+                    help="run eight learned global-move rounds (for the launch list of a round) and exit")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
+    if args.profile_global:
+        return profile_global()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
