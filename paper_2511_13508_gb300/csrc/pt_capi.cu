@@ -140,7 +140,7 @@ struct LearnState {
     int Mb = 0, ncap = 0, ndata = 0, nprop = 0, rows = 0, global_every = 0, adam_t = 0;
     bool one_launch = true;  // autoregressive sampling in one launch (nprop <= 64)
     cudaStream_t side = nullptr;  // the current configurations' density and energy, concurrent with the sampling
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_mid = nullptr, ev_join = nullptr;
     float *Ocur = nullptr;        // network outputs of the current configurations, laid out as O [S][rows][Dout]
     int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
@@ -500,7 +500,8 @@ DensityParams density_params(LearnState &L, const float *O, const RawRows &raw, 
 // One round of learned global moves on the chains at the ncold coldest temperatures of every sample.
 // When the network's forward pass fits one launch, the current configurations' density and energy run on a
 // second stream, concurrently with the sampling of the proposals (they share only the features X, which
-// neither side writes after the fork); the Metropolis-Hastings step waits for both.
+// neither side writes after the fork), and so does the proposals' energy, beside their features, forward
+// pass and density; the Metropolis-Hastings step waits for both streams.
 int run_global(pt_ctx *c) {
     LearnState &L = *c->learn;
     const ptgb::LearnShape &sh = L.sh;
@@ -529,7 +530,6 @@ int run_global(pt_ctx *c) {
         EnergyList2 e1{};
         e1.set[0] = ep;
         CK(launch_energy_list(e1, 1, c->S, L.side));
-        CK(cudaEventRecord(L.ev_join, L.side));
     } else {
         if ((rc = learn_forward(c, L.X, np, L.pcond, np, false)) != PT_OK) return rc;
         DensityParams dc = density_params(L, L.O, L.rcur, L.lq_cur, np, false);
@@ -565,6 +565,17 @@ int run_global(pt_ctx *c) {
     ap.row_id = L.prow; ap.ctl = c->d_ctl; ap.a = L.a_prop;
     ap.a_cur = c->d_a; ap.dbl = c->dbl ? 1 : 0; ap.samples = c->d_samples; ap.slot = L.pslot;
     CK(launch_assemble(ap, c->S, c->stream));
+    EnergyListParams &eq = el.set[1];
+    eq = ep;
+    eq.a = L.a_prop; eq.dbl = 1; eq.slot = nullptr; eq.E = L.H_prop;
+    if (split) {  // the proposals' energy on the side stream too, beside their features, forward pass and density
+        CK(cudaEventRecord(L.ev_mid, c->stream));
+        CK(cudaStreamWaitEvent(L.side, L.ev_mid, 0));
+        EnergyList2 e2{};
+        e2.set[0] = eq;
+        CK(launch_energy_list(e2, 1, c->S, L.side));
+        CK(cudaEventRecord(L.ev_join, L.side));
+    }
     // proposed configurations as stored: features (into Xp: the side stream may still read X), density, energy
     FeatParams fq = fp;
     fq.a = L.a_prop; fq.dbl = 1; fq.slot = nullptr; fq.raw = L.rprop; fq.X = L.Xp;
@@ -572,13 +583,7 @@ int run_global(pt_ctx *c) {
     if ((rc = learn_forward(c, L.Xp, np, L.pcond, np, false)) != PT_OK) return rc;
     DensityParams dq = density_params(L, L.O, L.rprop, L.lq_prop, np, false);
     CK(launch_density(dq, c->S, c->stream));
-    EnergyListParams &eq = el.set[1];
-    eq = ep;
-    eq.a = L.a_prop; eq.dbl = 1; eq.slot = nullptr; eq.E = L.H_prop;
     if (split) {
-        EnergyList2 e2{};
-        e2.set[0] = eq;
-        CK(launch_energy_list(e2, 1, c->S, c->stream));
         CK(cudaStreamWaitEvent(c->stream, L.ev_join, 0));
     } else {
         CK(launch_energy_list(el, 2, c->S, c->stream));  // both sets in one launch
@@ -1516,6 +1521,7 @@ int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_
     if (rc == PT_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_mid, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(c, e, "pt_learn_init: stream");
     }
@@ -1762,6 +1768,7 @@ int pt_destroy(pt_ctx *c) {
     if (c->learn) {
         if (c->learn->side) { cudaStreamSynchronize(c->learn->side); cudaStreamDestroy(c->learn->side); }
         if (c->learn->ev_fork) cudaEventDestroy(c->learn->ev_fork);
+        if (c->learn->ev_mid) cudaEventDestroy(c->learn->ev_mid);
         if (c->learn->ev_join) cudaEventDestroy(c->learn->ev_join);
         delete c->learn;
         c->learn = nullptr;

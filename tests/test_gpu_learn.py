@@ -170,6 +170,43 @@ def test_learn_eval_single_launch_forward_matches_oracle(N, rows):
         assert err.max() <= 2e-3 + 5e-5 * scale, (err.max(), scale)
 
 
+def test_many_conditions_take_the_global_bias_path():
+    """More than 64 temperature conditions: the single-launch forward reads the conditional biases C1 from
+    global memory instead of staging them in shared memory, and 70 proposal rows per sample exceed the
+    one-launch sampler (per-block launches).  Densities against the oracle; global moves stay exact (the
+    energies that chains taking a proposal carry are the oracle's)."""
+    import oracle
+    N, S, R, nT, ncold = 16, 1, 1, 72, 70
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    J = [0.05 * j for j in _couplings([N] * S)]
+    pt = pkg.PT([N] * S, J, temps, R, 9, precision="fp64")
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=2)
+    sh = pt.learn_shape()
+    rng = np.random.default_rng(70)
+    P = _randomise_outputs(pt.learn_params().astype(np.float64), sh, rng).astype(np.float32)
+    pt.set_learn_params(P)
+    rows = 100
+    a = _dirichlet(N, (S, rows), 0.5, rng).astype(np.complex64).astype(np.complex128)
+    cond = rng.integers(0, ncold, (S, rows)).astype(np.int32)
+    lq, ex, _ = pt.learn_eval(a, cond)
+    lq_o, _ = ol.logq(P[0].astype(np.float64), a[0], cond[0], N, sh["H"], ncold, 8, emulate_bf16=True)
+    err = np.abs(lq[0] - lq_o)
+    scale = np.abs(lq_o).max()
+    assert np.quantile(err, 0.95) <= 2e-3 + 1e-5 * scale and err.max() <= 2e-3 + 5e-5 * scale, (err.max(), scale)
+    pt.set_learn_params(_stick_breaking_biases(N, pt.learn_params().astype(np.float64), sh).astype(np.float32))
+    pt.set_global_blocks(4, 7)
+    a0, E0 = pt.state()
+    for _ in range(4):
+        pt.global_move()
+    a1, E1 = pt.state()
+    moved = np.any(a1.reshape(-1, N) != a0.reshape(-1, N), axis=1)
+    assert moved.sum() >= 4, moved.sum()
+    quads = oracle.enumerate_quads(N)
+    for c in np.flatnonzero(moved):
+        ref = oracle.energy(N, quads, J[0], a1.reshape(-1, N)[c])
+        assert abs(E1[c] - ref) <= 1e-13 * np.abs(J[0]).sum(), (c, E1[c], ref)
+
+
 def test_learn_eval_rejects_bad_arguments():
     S, N = 1, 16
     pt = pkg.PT([N], _couplings([N]), workload.geometric_ladder(0.5, 1.5, 2), 4, 1, precision="fp32")
