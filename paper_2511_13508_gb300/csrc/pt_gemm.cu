@@ -301,12 +301,14 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-// 16 bytes to the same shared-memory offset in block `rank` of the cluster
-__device__ __forceinline__ void st_cluster16(uint32_t local, uint32_t rank, uint4 v) {
-    uint32_t remote;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(remote), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w)
+// Bulk copy of `bytes` from this block's shared memory at `local` to the same offset in block `rank` of the
+// cluster, completing (complete_tx) on the mbarrier at the same offset as `bar` in that block.
+__device__ __forceinline__ void bulk_s2peer(uint32_t local, uint32_t bytes, uint64_t *bar, uint32_t rank) {
+    uint32_t dst, rbar;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(local), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(smem_addr(bar)), "r"(rank));
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "r"(local), "r"(bytes), "r"(rbar)
                  : "memory");
 }
 
@@ -348,7 +350,7 @@ template <bool kSampler>
 __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     mlp_cluster_kernel(MlpParams p, SamplerExtra sx) {
     extern __shared__ __align__(1024) unsigned char msm[];
-    __shared__ uint64_t full[3], done;
+    __shared__ uint64_t full[3], done, xchg[2];  // weights; MMA completion; H1 / H2 slices from the peers
     __shared__ uint32_t tmem_base_slot;
     __shared__ float bsl[3][64];  // this block's slices of b1, b2, b3
     const uint32_t rank = cluster_rank();
@@ -381,6 +383,8 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     if (threadIdx.x == 0) {
         for (int l = 0; l < 3; ++l) mbar_init1(&full[l]);
         mbar_init1(&done);
+        mbar_init1(&xchg[0]);
+        mbar_init1(&xchg[1]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -439,7 +443,6 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
             uint32_t r[32];
             if (l < 2) {
                 if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-                if (first_wait && l == 0) cluster_wait();  // all blocks of the cluster have started
                 if (quad * 32 < Mp && row < Mp && ok) {
                     const bool live = row < p.M;
                     const float *cb = (l == 0 && live) ? (stage_c1 ? c1s + cond[row] * NS + c0
@@ -464,14 +467,24 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
                             w[e] = *reinterpret_cast<const uint32_t *>(&h);
                         }
                         const uint32_t kg = (uint32_t)(rank * NS + c0 + 8 * g) / 8;
-                        const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
-                        for (uint32_t dstr = 0; dstr < (uint32_t)kMlpCL; ++dstr) st_cluster16(dst + kg * lboA, dstr, v);
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kg * lboA), "r"(w[0]),
+                                     "r"(w[1]), "r"(w[2]), "r"(w[3])
+                                     : "memory");
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");  // generic writes -> tensor core reads
+                // the slice (K-groups [rank NS/8, (rank+1) NS/8), contiguous) goes to the peers by bulk copies that
+                // complete on their exchange barrier; this block's own copy is read by its tensor cores
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                cluster_arrive();
-                cluster_wait();
+                __syncthreads();
+                if (first_wait && l == 0) cluster_wait();  // all blocks of the cluster have started
+                const uint32_t slice = (uint32_t)(NS / 8) * lboA;
+                if (threadIdx.x == 0) {
+                    mbar_expect_tx(&xchg[l], (uint32_t)(kMlpCL - 1) * slice);
+                    const uint32_t src = (l == 0 ? sH1 : sH2) + rank * slice;
+                    for (uint32_t q = 1; q < (uint32_t)kMlpCL; ++q) bulk_s2peer(src, slice, &xchg[l], (rank + q) % kMlpCL);
+                }
+                if (!mbar_wait(&xchg[l], (uint32_t)(pass - pass0) & 1u)) ok = false;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             } else if (!kSampler) {
                 if (quad * 32 < Mp) tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
@@ -530,6 +543,10 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
             }
         }
         first_wait = false;
+    }
+    if (!kSampler) {  // the peers' bulk copies out of this block's shared memory are complete before it exits
+        cluster_arrive();
+        cluster_wait();
     }
     if (!ok && threadIdx.x == 0) {
         if (p.err) atomicCAS(p.err, 0, kErrTimeout);

@@ -123,8 +123,8 @@ __global__ void features_kernel(FeatParams p) {
 
 cudaError_t launch_features(const FeatParams &p, int S, cudaStream_t s) {
     if (p.rows_per_sample <= 0) return cudaSuccess;
-    dim3 grid((p.rows_per_sample + 1) / 2, S);  // two rows per block: the FP64 work spread over many SMs
-    features_kernel<<<grid, 64, 0, s>>>(p);
+    dim3 grid(p.rows_per_sample, S);  // one row (warp) per block: the FP64 work spread over all SMs
+    features_kernel<<<grid, 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -222,8 +222,8 @@ __global__ void density_kernel(DensityParams p) {
 
 cudaError_t launch_density(const DensityParams &p, int S, cudaStream_t s) {
     if (p.rows_per_sample <= 0) return cudaSuccess;
-    dim3 grid((p.rows_per_sample + 3) / 4, S);
-    density_kernel<<<grid, 128, 0, s>>>(p);
+    dim3 grid(p.rows_per_sample, S);  // one row (warp) per block
+    density_kernel<<<grid, 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -435,8 +435,8 @@ __global__ void assemble_kernel(AssembleParams p) {
 }
 
 cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
-    dim3 grid((p.rows_per_sample + 3) / 4, S);
-    assemble_kernel<<<grid, 128, 0, s>>>(p);
+    dim3 grid(p.rows_per_sample, S);  // one row (warp) per block: the FP64 work spread over all SMs
+    assemble_kernel<<<grid, 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
