@@ -142,6 +142,7 @@ struct LearnState {
     cudaStream_t side = nullptr;  // the current configurations' density and energy, concurrent with the sampling
     cudaEvent_t ev_fork = nullptr, ev_mid = nullptr, ev_join = nullptr;
     float *Ocur = nullptr;        // network outputs of the current configurations, laid out as O [S][rows][Dout]
+    float2 *Jdf = nullptr;        // FP32 chains: the couplings of the quadruplet lists as float pairs
     int blk_lo = 0, blk_hi = ptgb::kLearnBlocks - 1;  // range of the first resampled block
     uint32_t step = 0;
     uint64_t seed = 0;
@@ -517,7 +518,7 @@ int run_global(pt_ctx *c) {
     EnergyList2 el{};
     EnergyListParams &ep = el.set[0];
     ep.a = c->d_a; ep.dbl = c->dbl ? 1 : 0; ep.samples = c->d_samples; ep.slot = L.pslot; ep.rows_per_sample = np;
-    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
+    ep.N = sh.N; ep.quads = c->d_quads; ep.Jq = c->d_Jq; ep.Jdf = L.Jdf; ep.cc = c->cfg.cc_factor; ep.E = L.H_cur;
     MlpParams mc = mlp_params(c, L.X, np, L.pcond, np);
     mc.O = L.Ocur;
     const bool split = fused_mlp_supported(mc, false);
@@ -1518,6 +1519,12 @@ int pt_learn_init(pt_ctx *c, int n_cold, int batch, int data_per_sample, uint64_
     L->prow = lalloc<uint32_t>(c, S * L->nprop, &rc);
     L->a_prop = lalloc<double2>(c, S * L->nprop * N, &rc);
     L->Ocur = lalloc<float>(c, S * rows * sh.Dout, &rc);  // the strides of O
+    if (!c->dbl) {
+        int64_t nq_total = 0;
+        for (const auto &sd : c->samples) nq_total = std::max<int64_t>(nq_total, sd.q_off + sd.nq);
+        L->Jdf = lalloc<float2>(c, std::max<int64_t>(nq_total, 1), &rc);
+        if (rc == PT_OK) CK(launch_split_df(c->d_Jq, L->Jdf, nq_total, c->stream));
+    }
     if (rc == PT_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming);

@@ -441,21 +441,70 @@ cudaError_t launch_assemble(const AssembleParams &p, int S, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Index of the pair (x, y), x < y, in the row-by-row upper triangle of an N x N table.
-__device__ __forceinline__ int tri_index(int x, int y, int N) { return x * (2 * N - x - 1) / 2 + (y - x - 1); }
+// Index of the pair (x, y), x < y, in a table of the upper triangle stored diagonal by diagonal: the pairs of
+// distance d = y - x are consecutive in x.  Consecutive quadruplets of the canonical order share their first
+// pair and step their second pair (z, z + d) along a diagonal, so the lanes of a warp read one entry and
+// consecutive entries (no shared-memory bank conflicts).
+__device__ __forceinline__ int tri_index(int x, int y, int N) {
+    const int d = y - x;
+    return (d - 1) * N - (d - 1) * d / 2 + x;
+}
 
-// FP64 energy H = -cc sum_q J_q Re(conj(a_x) a_y a_z conj(a_w)) of one row per block; blockIdx.z picks one
-// of two row sets (the current configurations and the proposals of a round, in one launch).
-//  - The pair products P(x, y) = conj(a_x) a_y, x < y, are tabulated in shared memory (upper triangle,
-//    N(N-1)/2 entries, 31.5 KB at N = 64, so that the launch's blocks fit on the GPU in one wave); a pair given
-//    in the other order is the conjugate, a sign flip done on the bits.  Each term is then
-//    J_q Re(P(x, y) conj P(z, w)): three FP64 operations per quadruplet instead of nine, which matters on a part
-//    whose FP64 rate is a small fraction of its FP32 rate.
-//  - Summing runs of quadruplets that share their first pair before multiplying by P(x, y) would save another
-//    third of the operations, but the run boundaries differ between the lanes of a warp and the divergent
-//    flushes cost the whole warp: it measured slower.
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two floats, ~48 significant bits) from
+// the error-free transformations: Knuth's two-sum and the FMA form of Dekker's two-product.
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// Re(u conj w) = u.re w.re + u.im w.im for double-float u = (re, im), w = (re, im) (float4: re.hi, re.lo,
+// im.hi, im.lo)
+__device__ __forceinline__ dfloat df_dot2(float4 u, float4 w) {
+    const dfloat p1 = two_prod(u.x, w.x), p2 = two_prod(u.z, w.z);
+    const dfloat s = two_sum(p1.hi, p2.hi);
+    float lo = __fadd_rn(p1.lo, p2.lo);
+    lo = __fmaf_rn(u.x, w.y, lo);
+    lo = __fmaf_rn(u.y, w.x, lo);
+    lo = __fmaf_rn(u.z, w.w, lo);
+    lo = __fmaf_rn(u.w, w.z, lo);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, lo));
+}
+// conj(a_x) a_y for FP32 amplitudes, each component exact as a two-product pair, summed to double-float
+__device__ __forceinline__ float4 df_pair(float2 ax, float2 ay) {
+    const dfloat r1 = two_prod(ax.x, ay.x), r2 = two_prod(ax.y, ay.y);   // re = ax.x ay.x + ax.y ay.y
+    const dfloat i1 = two_prod(ax.x, ay.y), i2 = two_prod(-ax.y, ay.x);  // im = ax.x ay.y - ax.y ay.x
+    const dfloat rs = two_sum(r1.hi, r2.hi), is = two_sum(i1.hi, i2.hi);
+    const dfloat re = fast_two_sum(rs.hi, __fadd_rn(rs.lo, __fadd_rn(r1.lo, r2.lo)));
+    const dfloat im = fast_two_sum(is.hi, __fadd_rn(is.lo, __fadd_rn(i1.lo, i2.lo)));
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// Energy H = -cc sum_q J_q Re(conj(a_x) a_y a_z conj(a_w)) of one row per block; blockIdx.z picks one of two
+// row sets (the current configurations and the proposals of a round).
+//  - The pair products P(x, y) = conj(a_x) a_y, x < y, are tabulated in shared memory (upper triangle by
+//    diagonals, N(N-1)/2 entries of 16 bytes, 31.5 KB at N = 64, so that a launch's blocks fit in one wave);
+//    a pair given in the other order is the conjugate, a sign flip done on the bits.  Each term is then
+//    J_q Re(P(x, y) conj P(z, w)).
+//  - kDF (FP32 configurations): P in double-float from exact two-products, the terms and the running sum
+//    of a thread in double-float (about 30 FP32 operations per quadruplet), the threads' sums added in
+//    FP64.  GB300 runs FP32 at many times its FP64 rate, and the sum stays within ~1e-14 of the FP64 one.
+//  - otherwise FP64: three operations per quadruplet (nine for the direct product).
+//  - Summing runs of quadruplets that share their first pair before multiplying by P(x, y) would save a
+//    third of the FP64 operations, but the run boundaries differ between the lanes of a warp and the
+//    divergent flushes cost the whole warp: it measured slower.
+template <bool kDF>
 __global__ void __launch_bounds__(256) energy_list_kernel(EnergyList2 pp) {
-    extern __shared__ double2 pairs[];  // [N (N - 1) / 2]
+    extern __shared__ double2 pairs[];  // [N (N - 1) / 2] (as float4 (re.hi, re.lo, im.hi, im.lo) with kDF)
     __shared__ double2 sa[kLearnMaxN];
     __shared__ double red[8];
     const EnergyListParams &p = pp.set[blockIdx.z];
@@ -477,24 +526,60 @@ __global__ void __launch_bounds__(256) energy_list_kernel(EnergyList2 pp) {
     }
     __syncthreads();
     for (int e = threadIdx.x; e < N * (N - 1) / 2; e += blockDim.x) {
-        int x = 0, rem = e;  // e -> (x, y), x < y
-        while (rem >= N - 1 - x) { rem -= N - 1 - x; ++x; }
-        const int y = x + 1 + rem;
+        int d = 1, rem = e;  // e -> diagonal d, x (the inverse of tri_index)
+        while (rem >= N - d) { rem -= N - d; ++d; }
+        const int x = rem, y = x + d;
         const double2 ax = sa[x], ay = sa[y];
-        pairs[e] = make_double2(ax.x * ay.x + ax.y * ay.y, ax.x * ay.y - ax.y * ay.x);
+        if (kDF)
+            reinterpret_cast<float4 *>(pairs)[e] =
+                df_pair(make_float2((float)ax.x, (float)ax.y), make_float2((float)ay.x, (float)ay.y));
+        else
+            pairs[e] = make_double2(ax.x * ay.x + ax.y * ay.y, ax.x * ay.y - ax.y * ay.x);
     }
     __syncthreads();
     const int4 *Q = p.quads + sd.q_off;
-    const double *J = p.Jq + sd.q_off;
     double acc = 0.0;
-    for (int64_t q = threadIdx.x; q < sd.nq; q += blockDim.x) {
-        const int4 t = Q[q];
-        const bool f1 = t.x > t.y, f2 = t.z > t.w;
-        const double2 u = pairs[f1 ? tri_index(t.y, t.x, N) : tri_index(t.x, t.y, N)];
-        const double2 w = pairs[f2 ? tri_index(t.w, t.z, N) : tri_index(t.z, t.w, N)];
-        // Im P(x, y) Im P(z, w) changes sign when exactly one of the two pairs was stored the other way round
-        const double wy = __longlong_as_double(__double_as_longlong(w.y) ^ ((long long)(f1 != f2) << 63));
-        acc = fma(J[q], fma(u.x, w.x, u.y * wy), acc);
+    if (kDF) {
+        const float2 *J = p.Jdf + sd.q_off;
+        const float4 *P4 = reinterpret_cast<const float4 *>(pairs);
+        float ahi = 0.f, alo = 0.f;
+        constexpr int kU = 4;  // quadruplets per batch: their loads are issued together (latency, not ALU, bounds)
+        for (int64_t q0 = threadIdx.x; q0 < sd.nq; q0 += (int64_t)kU * blockDim.x) {
+            int4 t[kU];
+            float2 j[kU];
+#pragma unroll
+            for (int i = 0; i < kU; ++i) {
+                const int64_t q = q0 + (int64_t)i * blockDim.x;
+                const bool in = q < sd.nq;
+                t[i] = in ? __ldg(Q + q) : make_int4(0, 1, 0, 1);
+                j[i] = in ? __ldg(J + q) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < kU; ++i) {
+                const bool f1 = t[i].x > t[i].y, f2 = t[i].z > t[i].w;
+                const float4 u = P4[f1 ? tri_index(t[i].y, t[i].x, N) : tri_index(t[i].x, t[i].y, N)];
+                float4 w = P4[f2 ? tri_index(t[i].w, t[i].z, N) : tri_index(t[i].z, t[i].w, N)];
+                if (f1 != f2) { w.z = -w.z; w.w = -w.w; }  // one of the pairs stored the other way round
+                const dfloat v = df_dot2(u, w);
+                const dfloat m = two_prod(j[i].x, v.hi);
+                const float mlo = __fmaf_rn(j[i].x, v.lo, __fmaf_rn(j[i].y, v.hi, m.lo));
+                const dfloat s1 = two_sum(ahi, m.hi);
+                ahi = s1.hi;
+                alo = __fadd_rn(alo, __fadd_rn(s1.lo, mlo));
+            }
+        }
+        acc = (double)ahi + (double)alo;
+    } else {
+        const double *J = p.Jq + sd.q_off;
+        for (int64_t q = threadIdx.x; q < sd.nq; q += blockDim.x) {
+            const int4 t = Q[q];
+            const bool f1 = t.x > t.y, f2 = t.z > t.w;
+            const double2 u = pairs[f1 ? tri_index(t.y, t.x, N) : tri_index(t.x, t.y, N)];
+            const double2 w = pairs[f2 ? tri_index(t.w, t.z, N) : tri_index(t.z, t.w, N)];
+            // Im P(x, y) Im P(z, w) changes sign when exactly one of the two pairs was stored the other way round
+            const double wy = __longlong_as_double(__double_as_longlong(w.y) ^ ((long long)(f1 != f2) << 63));
+            acc = fma(J[q], fma(u.x, w.x, u.y * wy), acc);
+        }
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
@@ -510,12 +595,27 @@ cudaError_t launch_energy_list(const EnergyList2 &p, int n_sets, int S, cudaStre
     int rows = 0;
     for (int i = 0; i < n_sets; ++i) {
         if (p.set[i].N < 1 || p.set[i].N > kLearnMaxN || p.set[i].N != p.set[0].N) return cudaErrorInvalidValue;
+        if ((p.set[i].Jdf != nullptr) != (p.set[0].Jdf != nullptr)) return cudaErrorInvalidValue;
         rows = std::max(rows, p.set[i].rows_per_sample);
     }
     if (rows <= 0) return cudaSuccess;
     const size_t sm = sizeof(double2) * (size_t)p.set[0].N * (p.set[0].N - 1) / 2;
     dim3 grid(rows, S, n_sets);
-    energy_list_kernel<<<grid, 256, sm, s>>>(p);
+    if (p.set[0].Jdf) energy_list_kernel<true><<<grid, 256, sm, s>>>(p);
+    else energy_list_kernel<false><<<grid, 256, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+__global__ void split_df_kernel(const double *J, float2 *Jdf, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float hi = (float)J[i];
+        Jdf[i] = make_float2(hi, (float)(J[i] - (double)hi));
+    }
+}
+
+cudaError_t launch_split_df(const double *J, float2 *Jdf, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    split_df_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(J, Jdf, n);
     return cudaGetLastError();
 }
 

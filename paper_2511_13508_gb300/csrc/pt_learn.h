@@ -151,13 +151,19 @@ struct EnergyListParams {
     int rows_per_sample, N;
     const int4 *quads;
     const double *Jq;
+    // FP32 configurations (values exact in FP32, also when given as double2): the sum in double-float
+    // arithmetic from the couplings split into float pairs Jdf (J = hi + lo), instead of FP64
+    const float2 *Jdf;
     double cc;
     double *E;               // [S][rows]
 };
 struct EnergyList2 {
     EnergyListParams set[2];
 };
+// All sets of one launch use the same arithmetic: double-float if set[0].Jdf is given, else FP64.
 cudaError_t launch_energy_list(const EnergyList2 &p, int n_sets, int S, cudaStream_t s);
+// Jdf[i] = (hi, lo) floats with hi + lo = J[i] to 48 bits.
+cudaError_t launch_split_df(const double *J, float2 *Jdf, int64_t n, cudaStream_t s);
 
 // Metropolis-Hastings decision and state update of every proposal row.
 struct MHParams {
