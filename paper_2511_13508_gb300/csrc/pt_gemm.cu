@@ -326,9 +326,12 @@ constexpr int kMlpMaxCond = 64;                     // conditions whose C1 colum
 __device__ __forceinline__ void mlp_mma(uint32_t tmem, uint32_t abuf, uint32_t lboA, uint32_t wbuf, int NS, int K,
                                        uint64_t *done) {
     const uint32_t idesc = make_idesc(NS), lboB = (uint32_t)NS * 16u;
+    // the start address (bits 0-13, in 16-byte units) advances by two K-groups per step; shared-memory
+    // addresses stay below 256 KB, so the field never carries
+    const uint64_t da0 = make_sdesc(abuf, lboA, 128), db0 = make_sdesc(wbuf, lboB, 128);
+    const uint64_t dda = (uint64_t)((2 * lboA) >> 4), ddb = (uint64_t)((2 * lboB) >> 4);
     for (int t = 0; t < K / 16; ++t) {
-        const uint64_t da = make_sdesc(abuf + (uint32_t)(2 * t) * lboA, lboA, 128);
-        const uint64_t db = make_sdesc(wbuf + (uint32_t)(2 * t) * lboB, lboB, 128);
+        const uint64_t da = da0 + (uint64_t)t * dda, db = db0 + (uint64_t)t * ddb;
         const uint32_t acc = t > 0 ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred pacc;\n\tsetp.ne.b32 pacc, %4, 0;\n\t"
@@ -370,7 +373,8 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     const bool stage_c1 = p.ncond <= kMlpMaxCond;
     float *c1s = reinterpret_cast<float *>(msm + (w0 - sH2) + wbytes[0] + wbytes[1] + wbytes[2]);
     float *obuf = c1s + (stage_c1 ? p.ncond * NS : 0);
-    int *fbs = reinterpret_cast<int *>(obuf + (kSampler ? Mp * 32 : 0));
+    ModeNoise *noise = reinterpret_cast<ModeNoise *>(obuf + (kSampler ? Mp * 32 : 0));  // [M][2 N/8]
+    int *fbs = reinterpret_cast<int *>(noise + (kSampler ? p.M * 2 * (sx.N / kLearnBlocks) : 0));
     const unsigned char *gW[3] = {
         reinterpret_cast<const unsigned char *>(p.W1c + (int64_t)b * p.strideW1) + (size_t)rank * wbytes[0],
         reinterpret_cast<const unsigned char *>(p.W2c + (int64_t)b * p.strideW2) + (size_t)rank * wbytes[1],
@@ -400,10 +404,17 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
         bsl[1][threadIdx.x] = P[p.ob2 + rank * NS + threadIdx.x];
         bsl[2][threadIdx.x] = threadIdx.x < NS3 ? P[p.ob3 + rank * NS3 + threadIdx.x] : 0.f;
     }
-    if (kSampler)
+    if (kSampler) {
+        const uint32_t rnd = (uint32_t)sx.ctl->global_rounds;
         for (int rw = threadIdx.x; rw < p.M; rw += blockDim.x)
-            fbs[rw] = first_block(sx.seed, sx.row_id[(int64_t)b * p.M + rw], (uint32_t)sx.ctl->global_rounds, sx.N,
-                                  sx.lo, sx.hi);
+            fbs[rw] = first_block(sx.seed, sx.row_id[(int64_t)b * p.M + rw], rnd, sx.N, sx.lo, sx.hi);
+        // the state-independent part of the draws of this block's modes (mode blocks 2 rank and 2 rank + 1)
+        const int per = sx.N / kLearnBlocks, nm = 2 * per;
+        for (int i = threadIdx.x; i < p.M * nm; i += blockDim.x) {
+            const int rw = i / nm, k = 2 * (int)rank * per + i % nm;
+            noise[i] = mode_noise(draw(sx.seed, sx.row_id[(int64_t)b * p.M + rw], rnd, (uint32_t)k, kTagGlobal));
+        }
+    }
     if (stage_c1)  // this block's columns of C1, all conditions
         for (int i = threadIdx.x; i < p.ncond * NS; i += blockDim.x)
             c1s[i] = P[p.oC1 + (int64_t)(i / NS) * p.H + rank * NS + i % NS];
@@ -417,8 +428,6 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
     const uint32_t tmem = tmem_base_slot;
     const int *cond = p.cond + (int64_t)b * p.strideCond;
     const int quad = warp % 4, part = warp / 4, row = quad * 32 + lane;
-    // sampler: the draws' round and each proposal row's first resampled block
-    const uint32_t round = kSampler ? (uint32_t)sx.ctl->global_rounds : 0u;
     bool ok = true;
     uint32_t n_commits = 0;
     const int pass0 = kSampler ? sx.lo : 0, pass1 = kSampler ? kLearnBlocks : 1;
@@ -513,21 +522,30 @@ __global__ void __cluster_dims__(kMlpCL, 1, 1) __launch_bounds__(kMlpThreads, 1)
                                 if (q < 4 * per) obuf[row * 32 + q] = __uint_as_float(r[q]) + bsl[2][c0 + q];
                     }
                     __syncthreads();
-                    for (int idx = threadIdx.x; idx < p.M * per && ok; idx += blockDim.x) {
-                        const int rw = idx / per, t = idx % per, k = pass * per + t;
+                    // item (row, mode, half): half 0 draws u (feature 0), half 1 draws phi~ (features 1, 2)
+                    for (int idx = threadIdx.x; idx < 2 * p.M * per && ok; idx += blockDim.x) {
+                        const int half = idx & 1, rw = (idx >> 1) / per, t = (idx >> 1) % per, k = pass * per + t;
                         if (pass < fbs[rw]) continue;
                         const int64_t gr = (int64_t)b * p.M + rw;
-                        const float o[4] = {obuf[rw * 32 + 4 * t], obuf[rw * 32 + 4 * t + 1], obuf[rw * 32 + 4 * t + 2],
-                                            obuf[rw * 32 + 4 * t + 3]};
-                        const u32x4 w = draw(sx.seed, sx.row_id[gr], round, (uint32_t)k, kTagGlobal);
-                        float u, ph;
-                        sample_mode(o, w, k, sx.N, &u, &ph);
-                        sx.u[gr * sx.N + k] = u;
-                        sx.phi[gr * sx.N + k] = ph;
-                        float f[3];
-                        feature_triplet(u, ph, k, sx.N, f);
-                        for (int c = 0; c < 3; ++c) {
-                            const uint32_t fi = (uint32_t)(3 * k + c);
+                        const ModeNoise nz = noise[rw * 2 * per + (pass % 2) * per + t];
+                        const float *o = obuf + rw * 32 + 4 * t;
+                        float f[2];
+                        int nf, f0;
+                        if (half == 0) {
+                            const float u = sample_u(o[0], o[1], nz.eps, k, sx.N);
+                            sx.u[gr * sx.N + k] = u;
+                            f[0] = feature_u(u, k, sx.N);
+                            nf = 1; f0 = 0;
+                        } else {
+                            const float ph = sample_phi(o[2], o[3], nz.t1, k);
+                            sx.phi[gr * sx.N + k] = ph;
+                            float sn, cs;
+                            sincosf(ph, &sn, &cs);
+                            f[0] = cs; f[1] = sn;
+                            nf = 2; f0 = 1;
+                        }
+                        for (int c = 0; c < nf; ++c) {
+                            const uint32_t fi = (uint32_t)(3 * k + f0 + c);
                             const __nv_bfloat16 h = __float2bfloat16_rn(f[c]);
                             const uint16_t bits = *reinterpret_cast<const uint16_t *>(&h);
                             const uint32_t off = sX + (fi / 8) * lboA + (uint32_t)rw * 16u + (fi % 8) * 2u;
@@ -573,7 +591,7 @@ size_t mlp_cluster_smem(const MlpParams &p, bool sampler) {
     if (sampler) act += (size_t)(p.Din / 8) * Mp * 16 + kMlpPad;
     const size_t w = ((size_t)p.Din + p.H) * (p.H / kMlpCL) * 2 + (size_t)p.H * (p.Dout / kMlpCL) * 2;
     size_t extra = p.ncond <= kMlpMaxCond ? (size_t)p.ncond * (p.H / kMlpCL) * 4 : 0;
-    if (sampler) extra += Mp * 32 * 4 + (size_t)p.M * 4;
+    if (sampler) extra += Mp * 32 * 4 + (size_t)p.M * 2 * (p.Dout / 4 / kLearnBlocks) * sizeof(ModeNoise) + (size_t)p.M * 4;
     return act + w + extra <= kMlpSmemMax ? act + w + extra : 0;
 }
 
