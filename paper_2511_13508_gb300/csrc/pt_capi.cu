@@ -537,10 +537,8 @@ int run_global(pt_ctx *c) {
         CK(launch_density(dc, c->S, c->stream));
     }
     // autoregressive sampling, one pass per block of modes from the first resampled block of each row on;
-    // the blocks below it keep the current configuration's features and variables
-    CK(cudaMemcpyAsync(L.rsamp.u, L.rcur.u, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(L.rsamp.phi, L.rcur.phi, sizeof(float) * (size_t)c->S * np * sh.N, cudaMemcpyDeviceToDevice,
-                       c->stream));
+    // the blocks below it keep the current configuration's features (the assembly copies their amplitudes
+    // from the current configuration and reads the drawn variables only from the first resampled mode on)
     const MlpParams ms = mlp_params(c, L.X, np, L.pcond, np);
     if (L.one_launch && fused_mlp_supported(ms, true)) {  // all passes in one launch, weights resident on chip
         SamplerExtra sx{};
