@@ -150,3 +150,42 @@ def test_sparse_graphs_beyond_the_comb_size_limit(prec):
         Eo = [oracle.energy(n, g, J, x) for (n, g, J), x in zip(per, xs)]
         assert np.allclose(E1, Eo, rtol=1e-4, atol=1e-3)
         assert np.allclose([(np.abs(x) ** 4).sum() / len(x) for x in xs], 1.0, rtol=1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64_plain"])
+def test_learned_global_moves_on_the_random_graph(prec):
+    """Learned global moves on the random-frequency graph, whose quadruplets (p, u, v, q) hold pairs in either
+    order (the proposal-energy kernel then reads the conjugate of a tabulated pair product): chains that
+    take a proposal carry the oracle's energy of the configuration they hold, for the FP32 group kernels
+    (double-float energies) and the FP64 quadruplet-list path (FP64 energies)."""
+    from scipy import special
+    N, S, R, nT, ncold = 32, 2, 4, 4, 4
+    graphs, Js = _graphs([N] * S, 1300)
+    assert any(np.any((g[:, 0] > g[:, 1]) | (g[:, 2] > g[:, 3])) for g in graphs)  # reversed pairs occur
+    Js = [0.05 * J for J in Js]
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    pt = pkg.PT([N] * S, Js, temps, R, 41, precision=prec, graphs=graphs)
+    pt.learn_init(n_cold=ncold, batch=128, data_per_sample=128, seed=4)
+    sh = pt.learn_shape()
+    # output biases near the stick-breaking law of the beta = 0 distribution, so that proposals get accepted
+    P = pt.learn_params().astype(np.float64)
+    k = np.arange(N)
+    bb = np.maximum((N - k - 1) / 2, 0.5)
+    b3 = np.zeros((N, 4))
+    b3[:, 0] = special.digamma(0.5) - special.digamma(bb)
+    b3[:, 1] = 0.5 * np.log(special.polygamma(1, 0.5) + special.polygamma(1, bb))
+    b3[:, 3] = -6.0
+    P[:, sh["ob3"]:sh["ob3"] + 4 * N] = b3.ravel()
+    pt.set_learn_params(P.astype(np.float32))
+    pt.set_global_blocks(5, 7)
+    a0, E0 = pt.state()
+    for _ in range(12):
+        pt.global_move()
+    a1, E1 = pt.state()
+    moved = np.any(a1.reshape(-1, N) != a0.reshape(-1, N), axis=1)
+    assert moved.sum() >= 8, moved.sum()
+    assert np.array_equal(E1[~moved], E0[~moved])
+    for c in np.flatnonzero(moved):
+        s = int(c) // (R * nT)
+        ref = oracle.energy(N, graphs[s], Js[s], a1.reshape(-1, N)[c])
+        assert abs(E1[c] - ref) <= 1e-13 * np.abs(Js[s]).sum(), (c, E1[c], ref)
