@@ -923,10 +923,13 @@ __global__ void fields_kernel(FieldsParams prm) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Full energy (resync).  With the half fields h^+_x = sum_{m > x} conj(a_m) acc_x[x+m],
-//     H = -(cc/2) sum_x Re( conj(a_x) h^+_x ),
-// which visits every quadruplet twice (once per pair).  Products and row sums in `real`, per-block
-// sums accumulated in FP64.  With renorm != 0 the chain is first rescaled onto sum |a|^4 = N.
+// Full energy (resync).  With the partial fields h^>_x = sum_{m > x} conj(a_m) acc^>_x[x+m], where acc^>
+// keeps only the pairs {p, q} of row x+m whose smaller mode (the block column) exceeds x,
+//     H = -cc sum_x Re( conj(a_x) h^>_x ),
+// which visits every quadruplet once, at its smallest mode x (partner m: the largest; the pair {p, q} of
+// the two middle modes has p > x).  Blocks whose columns all lie at or below x are skipped.  Products and
+// row sums in `real`, per-block sums accumulated in FP64.  With renorm != 0 the chain is first rescaled
+// onto sum |a|^4 = N.
 template <typename real, int G>
 __global__ void energy_kernel(EnergyParams prm) {
     using V = typename vec2<real>::type;
@@ -989,6 +992,7 @@ __global__ void energy_kernel(EnergyParams prm) {
         const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
         const real *Jx = J + (sd.J_off + mode_blk[x] + (b - bo[stlo])) * JStride<real>::value;
         const int s0 = st * TS, x0 = xt * TX;
+        if (x0 + TX - 1 <= x) continue;  // every pair of the block has its smaller mode <= x
         V ax[TX], ay[TS + TX - 1], acc[TS];
 #pragma unroll
         for (int i = 0; i < TX; ++i) ax[i] = as[(x0 + i + APAD) * RS + c];
@@ -999,6 +1003,7 @@ __global__ void energy_kernel(EnergyParams prm) {
         for (int r = 0; r < TS; ++r) acc[r].x = acc[r].y = real(0);
 #pragma unroll
         for (int i = 0; i < TX; ++i) {
+            if (x0 + i <= x) continue;  // pairs whose smaller mode is <= x: counted at that mode
             JRow<real> jc;
             jc.load(Jx + i * TS);
 #pragma unroll
@@ -1022,7 +1027,7 @@ __global__ void energy_kernel(EnergyParams prm) {
     if (tid < gr.count) {
         double t = 0.0;
         for (int w = 0; w < NCW; ++w) t += dred[w * G + tid];
-        const double E = -0.5 * prm.cc * t;
+        const double E = -prm.cc * t;
         if (!isfinite(E)) record_error(prm.ctl, kErrNaN, 11);
         if (prm.E_out) prm.E_out[gr.chain0 + tid] = E;
         if (prm.E_state) prm.E_state[gr.chain0 + tid] = E;
