@@ -411,12 +411,30 @@ __global__ void assemble_kernel(AssembleParams p) {
             continue;
         }
         const double sk = r0 * P[q] * v[q];
-        const double A = sqrt(sqrt(n * fmax(sk, 0.0)));
         // phi~_k = phi_k - phi_0 - k (phi_1 - phi_0): errors in the phases of modes 0 and 1 come back k-fold
         // when the density is evaluated on the stored configuration, so those two are formed in FP64; the
-        // others carry an FP32 rounding of the draw (as the stored draw itself does).  The unit vector is
-        // renormalised in FP64 so that |a_k|^4 = n s_k holds to FP64 rounding.
+        // others carry an FP32 rounding of the draw (as the stored draw itself does).
         double ph = (double)p.phi[grow * N + k] + alpha + (double)k * theta;
+        if (!p.dbl) {
+            // FP32 chains store the proposal rounded to FP32 (its density and energy are taken of that
+            // rounding, the configuration the chain will hold), so the magnitude and the unit vector are
+            // formed in FP32; (n s)^(1/4) of very small values is taken after an exact scaling by 2^128
+            const double x = n * fmax(sk, 0.0);
+            const bool tiny = x < 0x1p-100;
+            const float Af = sqrtf(sqrtf((float)(tiny ? x * 0x1p128 : x))) * (tiny ? 0x1p-32f : 1.f);
+            if (k < 2) {
+                double sn, cs;
+                sincos(ph, &sn, &cs);
+                p.a[grow * N + k] = make_double2((float)((double)Af * cs), (float)((double)Af * sn));
+            } else {
+                float sf, cf;
+                sincosf((float)(ph - kTwoPi * floor(ph * (1.0 / kTwoPi))), &sf, &cf);
+                p.a[grow * N + k] = make_double2((double)(Af * cf), (double)(Af * sf));
+            }
+            continue;
+        }
+        // FP64 chains: the unit vector is renormalised in FP64 so that |a_k|^4 = n s_k holds to FP64 rounding
+        const double A = sqrt(sqrt(n * fmax(sk, 0.0)));
         double sn, cs;
         if (k < 2) {
             sincos(ph, &sn, &cs);
@@ -428,9 +446,7 @@ __global__ void assemble_kernel(AssembleParams p) {
             sn = sf * inv;
             cs = cf * inv;
         }
-        // FP32 chains store the proposal rounded to FP32: its density and energy are taken of that rounding,
-        // the configuration the chain will hold
-        p.a[grow * N + k] = p.dbl ? make_double2(A * cs, A * sn) : make_double2((float)(A * cs), (float)(A * sn));
+        p.a[grow * N + k] = make_double2(A * cs, A * sn);
     }
 }
 
