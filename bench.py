@@ -414,6 +414,34 @@ def profile_global():
     return 0
 
 
+def profile_graph():
+    """The graph legs' FP32 group kernels, a few launches each: the N=64 random-frequency graph (16 samples x
+    32 T x 2 replicas, 2 sweeps per launch) and the N=2048 sparse comb graph (z = 16, 1 sweep per launch)."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    pkg.build()
+    S, R = 16, 2
+    temps = workload.geometric_ladder(0.3, 1.6, 32)
+    kw = dict(swap_every=0, measure_every=0, resync_every=0, use_graphs=False)
+    graphs = [pkg.fmc_graph(workload.random_frequencies(64, 500 + s)) for s in range(S)]
+    Js = [workload.couplings(64, len(g), 600 + s) for s, g in enumerate(graphs)]
+    pt = pkg.PT([64] * S, Js, temps, R, 31, precision="fp32", graphs=graphs, **kw)
+    for _ in range(3):
+        pt.sweep(2)
+    pt.sync()
+    pt.close()
+    sg = [workload.sparse_comb_graph(2048, 16, 700 + s) for s in range(S)]
+    sJ = [workload.couplings(2048, len(g), 800 + s) * 2048 for s, g in enumerate(sg)]
+    pt = pkg.PT([2048] * S, sJ, temps, R, 37, precision="fp32", graphs=sg, **kw)
+    for _ in range(2):
+        pt.sweep(1)
+    pt.sync()
+    pt.close()
+    print("profile graph done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,11 +456,15 @@ def main():
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     ap.add_argument("--profile-global", action="store_true",
                     help="run eight learned global-move rounds (for the launch list of a round) and exit")
+    ap.add_argument("--profile-graph", action="store_true",
+                    help="a few launches of the graph kernels (N=64 random graph, N=2048 sparse graph) and exit")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
     if args.profile_global:
         return profile_global()
+    if args.profile_graph:
+        return profile_graph()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
