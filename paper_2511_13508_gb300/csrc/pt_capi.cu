@@ -173,6 +173,7 @@ struct pt_ctx {
     uint64_t seed = 0;
     bool dbl = false, plain = false;
     bool gfp32 = false;  // explicit interaction lists on the FP32 group kernels
+    int max_deg = 0;     // largest number of quadruplets holding one mode (quadruplet-list paths)
     cudaStream_t stream = nullptr;
     pt_alloc_fn alloc = nullptr;
     pt_free_fn free_ = nullptr;
@@ -284,7 +285,8 @@ int watchdog_sync(pt_ctx *c) {
 GraphParams graph_params(pt_ctx *c) {
     GraphParams p{};
     p.samples = c->d_samples; p.groups = c->d_groups; p.quads = c->d_quads; p.Jd = c->d_Jq;
-    p.inc_off = c->d_inc_off; p.rec = c->d_rec; p.recJ = c->d_recJ; p.a = reinterpret_cast<float2 *>(c->d_a);
+    p.inc_off = c->d_inc_off; p.max_deg = c->max_deg; p.rec = c->d_rec; p.recJ = c->d_recJ;
+    p.a = reinterpret_cast<float2 *>(c->d_a);
     p.E = c->d_E; p.label = c->d_label; p.beta = c->d_beta; p.mc_acc = c->d_mc_acc; p.mc_att = c->d_mc_att;
     p.R = c->R; p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
     p.measure_every = c->cfg.measure_every; p.snap_a = reinterpret_cast<float2 *>(c->d_snap_a);
@@ -984,6 +986,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
                 hJq[sd.q_off + q] = J[J_offsets[s] + q];
                 for (int m = 0; m < 4; ++m) deg[abcd[4 * q + m] + 1]++;
             }
+            for (int l = 0; l < n; ++l) c->max_deg = std::max(c->max_deg, deg[l + 1]);
             for (int l = 0; l < n; ++l) deg[l + 1] += deg[l];
             std::vector<int> fill(n, 0);
             for (int64_t q = 0; q < cnt; ++q)

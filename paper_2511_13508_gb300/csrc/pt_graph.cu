@@ -62,8 +62,13 @@ __device__ __forceinline__ GraphProposal graph_proposal(uint64_t seed, uint32_t 
 
 }  // namespace
 
+// kFew: every update's two record lists fit the workers (at most one record each, sparse graphs).  An
+// update is then bound by its fixed latencies, and the kernel trims them: the record offsets sit in shared
+// memory, each worker loads its record of the next update while the current one is reduced (the pairs and
+// the records do not depend on the state), and the leaders sum only the warps that held records.
+template <bool kFew>
 __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
-    extern __shared__ float2 ga[];  // [maxN][kGRS]
+    extern __shared__ float2 ga[];  // [maxN][kGRS] (kFew: then the sample's record offsets [N + 1])
     __shared__ float red[kGWarps][kGG][5];
     __shared__ GraphProposal prop[kGG];
     const GroupDev gr = p.groups[blockIdx.x];
@@ -87,18 +92,45 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
         beta = (float)p.beta[t];
         cid = (uint32_t)((gr.sample * p.R + r) * p.nT + t);
     }
-    const int *inc_off = p.inc_off + sd.mode_off;
+    int *inc_off_s = reinterpret_cast<int *>(ga + (size_t)p.maxN * kGRS);
+    if (kFew)
+        for (int i = tid; i <= N; i += kGThreads) inc_off_s[i] = p.inc_off[sd.mode_off + i];
+    const int *inc_off = kFew ? inc_off_s : p.inc_off + sd.mode_off;
     const int4 *rec = p.rec + sd.inc_off;
     const float *recJ = p.recJ + sd.inc_off;
     const float cc_f = (float)p.cc;
     const long long base = p.ctl->sweep_base;
     __syncthreads();
+    // kFew: the pair of the next update and this worker's record of it
+    int jn = 0, kn = 0;
+    int4 R4n = make_int4(0, 0, 0, 0);
+    float Jn = 0.f;
+    auto prefetch = [&](uint32_t sweep, uint32_t u) {
+        pair_jk(p.seed, (uint32_t)gr.sample, sweep, u, N, jn, kn);
+        const int oj = inc_off[jn], nj = inc_off[jn + 1] - oj, ok = inc_off[kn], nk = inc_off[kn + 1] - ok;
+        if (worker < nj + nk) {
+            const int r = worker < nj ? oj + worker : ok + worker - nj;
+            R4n = __ldg(rec + r);
+            Jn = __ldg(recJ + r);
+        }
+    };
+    if (kFew && p.n_sweeps > 0) prefetch((uint32_t)base, 0u);
     for (int sw = 0; sw < p.n_sweeps; ++sw) {
         const uint32_t sweep = (uint32_t)(base + sw);
         for (int u = 0; u < N / 2; ++u) {
             int j, k;
-            pair_jk(p.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
+            int4 R4f;
+            float Jf;
+            if (kFew) {
+                j = jn; k = kn; R4f = R4n; Jf = Jn;
+            } else {
+                pair_jk(p.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
+            }
             if (leader) prop[c] = graph_proposal(p.seed, cid, sweep, (uint32_t)u, ga[j * kGRS + c], ga[k * kGRS + c]);
+            if (kFew) {
+                if (u + 1 < N / 2) prefetch(sweep, (uint32_t)(u + 1));
+                else if (sw + 1 < p.n_sweeps) prefetch(sweep + 1u, 0u);
+            }
             __syncthreads();
             const GraphProposal P = prop[c];
             float2 hj = make_float2(0.f, 0.f), hk = make_float2(0.f, 0.f);
@@ -108,8 +140,8 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             for (int idx = worker; idx < nj + nk; idx += kGWorkers) {
                 const bool onj = idx < nj;
                 const int r = onj ? oj + idx : ok + idx - nj;
-                const int4 R4 = __ldg(rec + r);
-                const float J = __ldg(recJ + r);
+                const int4 R4 = kFew ? R4f : __ldg(rec + r);
+                const float J = kFew ? Jf : __ldg(recJ + r);
                 const int pos = R4.w & 3;         // position of the record's own mode (j or k)
                 const int other = onj ? k : j;    // the other updated mode, possibly among the three
                 const int o[3] = {R4.x, R4.y, R4.z};
@@ -157,7 +189,9 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             __syncthreads();
             if (leader && c < gr.count) {
                 float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int w = 0; w < kGWarps; ++w)
+                // kFew: warps whose workers held no record contribute exact zeros; only the others are summed
+                const int wmax = kFew ? min(kGWarps, (nj + nk + (32 / kGG) - 1) / (32 / kGG)) : kGWarps;
+                for (int w = 0; w < wmax; ++w)
 #pragma unroll
                     for (int e = 0; e < 5; ++e) t[e] += red[w][c][e];
                 // Re(conj(d) h) = d.x h.x + d.y h.y
@@ -269,17 +303,25 @@ __global__ void __launch_bounds__(kGThreads) graph_energy_kernel(GraphParams p) 
     }
 }
 
+// dynamic shared memory of the sweep kernel: amplitudes (72 B per mode) and record offsets (4 B per mode)
+static size_t graph_sweep_smem(int maxN) {
+    return (size_t)maxN * kGRS * sizeof(float2) + (size_t)(maxN + 1) * sizeof(int);
+}
+
 cudaError_t graph_prepare(int maxN) {
-    const int sm = maxN * kGRS * (int)sizeof(float2);  // 72 B per mode: 147 KB at N = 2048
-    cudaError_t e = cudaFuncSetAttribute(graph_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int sm = (int)graph_sweep_smem(maxN);  // 155 KB at N = 2048
+    cudaError_t e = cudaFuncSetAttribute(graph_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(graph_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return e;
 }
 
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s) {
     if (n_groups <= 0) return cudaSuccess;
-    const size_t sm = (size_t)p.maxN * kGRS * sizeof(float2);
-    graph_sweep_kernel<<<n_groups, kGThreads, sm, s>>>(p);
+    const size_t sm = graph_sweep_smem(p.maxN);
+    if (2 * p.max_deg <= kGWorkers) graph_sweep_kernel<true><<<n_groups, kGThreads, sm, s>>>(p);
+    else graph_sweep_kernel<false><<<n_groups, kGThreads, sm, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -125,6 +125,7 @@ struct GraphParams {
     const int4 *quads;       // quadruplets in term order, per sample at q_off (energy kernel)
     const double *Jd;        // FP64 couplings (energy kernel)
     const int *inc_off;      // per sample mode: offsets into the incidence records (N+1, at mode_off)
+    int max_deg;             // largest number of records of one mode, over all samples
     const int4 *rec;         // incidence records per mode (at inc_off): other three modes, (q << 2) | position
     const float *recJ;       // coupling of each incidence record
     float2 *a;
