@@ -44,7 +44,7 @@ extern "C" {
 #define PT_ETIMEOUT (-4)     /* a bounded device wait or the host watchdog ran out */
 #define PT_ENAN (-5)         /* non-finite coupling, or non-finite state found at resync */
 #define PT_ESTATE (-6)       /* checkpoint bytes do not match this context */
-#define PT_EUNSUPPORTED (-7) /* valid request this build does not implement */
+#define PT_EUNSUPPORTED (-7) /* valid request the library does not implement */
 
 /* ---------------------------------------------------------------- precision */
 #define PT_PREC_FP32 0       /* FP32 fields/moves, FP64 running energy, resync, swap log-ratio */
