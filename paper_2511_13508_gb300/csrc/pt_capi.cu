@@ -1066,7 +1066,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     CK(cudaMemset(c->d_qstat, 0, (size_t)S * n_T * PT_NQSTAT * sizeof(double)));
     CK(cudaMemset(c->d_ctl, 0, sizeof(Control)));
 
-    if (c->gfp32) CK(graph_prepare(c->maxN));
+    if (c->gfp32) CK(graph_prepare(c->maxN, c->max_deg));
     // ---- persistent grid
     if (!c->plain && !c->gfp32) {
         int dev = 0, sms = 0;

@@ -62,13 +62,35 @@ __device__ __forceinline__ GraphProposal graph_proposal(uint64_t seed, uint32_t 
 
 }  // namespace
 
-// kFew: every update's two record lists fit the workers (at most one record each, sparse graphs).  An
-// update is then bound by its fixed latencies, and the kernel trims them: the record offsets sit in shared
-// memory, each worker loads its record of the next update while the current one is reduced (the pairs and
-// the records do not depend on the state), and the leaders sum only the warps that held records.
-template <bool kFew>
+// Variants by how an update's records reach the workers:
+//  kPlain: each worker loads its records from global memory (L2) as it goes (the largest graphs).
+//  kFew: every update's two record lists fit the workers (at most one record each, sparse graphs).  An
+//    update is then bound by its fixed latencies, and the kernel trims them: the record offsets sit in
+//    shared memory, each worker loads its record of the next update while the current one is reduced (the
+//    pairs and the records do not depend on the state), and the leaders sum only the warps that held
+//    records.
+//  kStage: the two lists fit in shared memory; the whole block copies them there with asynchronous copies
+//    while the leaders draw the proposal (one L2 latency per update instead of one per record and worker).
+enum GraphVariant : int { kPlain = 0, kFew = 1, kStage = 2 };
+
+// Shared-memory layout of the sweep kernel: amplitudes [maxN][kGRS] float2, record offsets [maxN + 1] int,
+// then (kStage) the staged records [cap] int4 and couplings [cap] float.
+struct GraphSmem {
+    size_t inc, rec, J, total;
+};
+__host__ __device__ inline GraphSmem graph_smem(int maxN, int cap) {
+    GraphSmem g;
+    g.inc = (size_t)maxN * kGRS * sizeof(float2);
+    g.rec = (g.inc + (size_t)(maxN + 1) * sizeof(int) + 15) / 16 * 16;
+    g.J = g.rec + (size_t)cap * sizeof(int4);
+    g.total = g.J + (size_t)cap * sizeof(float);
+    return g;
+}
+
+template <int kVar>
 __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
-    extern __shared__ float2 ga[];  // [maxN][kGRS] (kFew: then the sample's record offsets [N + 1])
+    constexpr bool kFewV = kVar == kFew, kStageV = kVar == kStage;
+    extern __shared__ __align__(16) float2 ga[];  // laid out as graph_smem
     __shared__ float red[kGWarps][kGG][5];
     __shared__ GraphProposal prop[kGG];
     const GroupDev gr = p.groups[blockIdx.x];
@@ -92,10 +114,15 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
         beta = (float)p.beta[t];
         cid = (uint32_t)((gr.sample * p.R + r) * p.nT + t);
     }
-    int *inc_off_s = reinterpret_cast<int *>(ga + (size_t)p.maxN * kGRS);
-    if (kFew)
+    const int cap = 2 * p.max_deg;
+    const GraphSmem lay = graph_smem(p.maxN, kStageV ? cap : 0);
+    unsigned char *sbase = reinterpret_cast<unsigned char *>(ga);
+    int *inc_off_s = reinterpret_cast<int *>(sbase + lay.inc);
+    int4 *rec_s = reinterpret_cast<int4 *>(sbase + lay.rec);
+    float *recJ_s = reinterpret_cast<float *>(sbase + lay.J);
+    if (kFewV || kStageV)
         for (int i = tid; i <= N; i += kGThreads) inc_off_s[i] = p.inc_off[sd.mode_off + i];
-    const int *inc_off = kFew ? inc_off_s : p.inc_off + sd.mode_off;
+    const int *inc_off = (kFewV || kStageV) ? inc_off_s : p.inc_off + sd.mode_off;
     const int4 *rec = p.rec + sd.inc_off;
     const float *recJ = p.recJ + sd.inc_off;
     const float cc_f = (float)p.cc;
@@ -114,23 +141,35 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             Jn = __ldg(recJ + r);
         }
     };
-    if (kFew && p.n_sweeps > 0) prefetch((uint32_t)base, 0u);
+    if (kFewV && p.n_sweeps > 0) prefetch((uint32_t)base, 0u);
     for (int sw = 0; sw < p.n_sweeps; ++sw) {
         const uint32_t sweep = (uint32_t)(base + sw);
         for (int u = 0; u < N / 2; ++u) {
             int j, k;
             int4 R4f;
             float Jf;
-            if (kFew) {
+            if (kFewV) {
                 j = jn; k = kn; R4f = R4n; Jf = Jn;
             } else {
                 pair_jk(p.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
             }
+            if (kStageV) {  // the update's records into shared memory (the previous update's reads are done)
+                const int oj = inc_off[j], nj = inc_off[j + 1] - oj, ok = inc_off[k], nk = inc_off[k + 1] - ok;
+                for (int i = tid; i < nj + nk; i += kGThreads) {
+                    const int r = i < nj ? oj + i : ok + i - nj;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(rec_s + i)), "l"(rec + r)
+                                 : "memory");
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(recJ_s + i)), "l"(recJ + r)
+                                 : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             if (leader) prop[c] = graph_proposal(p.seed, cid, sweep, (uint32_t)u, ga[j * kGRS + c], ga[k * kGRS + c]);
-            if (kFew) {
+            if (kFewV) {
                 if (u + 1 < N / 2) prefetch(sweep, (uint32_t)(u + 1));
                 else if (sw + 1 < p.n_sweeps) prefetch(sweep + 1u, 0u);
             }
+            if (kStageV) asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
             const GraphProposal P = prop[c];
             float2 hj = make_float2(0.f, 0.f), hk = make_float2(0.f, 0.f);
@@ -140,8 +179,8 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             for (int idx = worker; idx < nj + nk; idx += kGWorkers) {
                 const bool onj = idx < nj;
                 const int r = onj ? oj + idx : ok + idx - nj;
-                const int4 R4 = kFew ? R4f : __ldg(rec + r);
-                const float J = kFew ? Jf : __ldg(recJ + r);
+                const int4 R4 = kFewV ? R4f : (kStageV ? rec_s[idx] : __ldg(rec + r));
+                const float J = kFewV ? Jf : (kStageV ? recJ_s[idx] : __ldg(recJ + r));
                 const int pos = R4.w & 3;         // position of the record's own mode (j or k)
                 const int other = onj ? k : j;    // the other updated mode, possibly among the three
                 const int o[3] = {R4.x, R4.y, R4.z};
@@ -190,7 +229,7 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             if (leader && c < gr.count) {
                 float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
                 // kFew: warps whose workers held no record contribute exact zeros; only the others are summed
-                const int wmax = kFew ? min(kGWarps, (nj + nk + (32 / kGG) - 1) / (32 / kGG)) : kGWarps;
+                const int wmax = kFewV ? min(kGWarps, (nj + nk + (32 / kGG) - 1) / (32 / kGG)) : kGWarps;
                 for (int w = 0; w < wmax; ++w)
 #pragma unroll
                     for (int e = 0; e < 5; ++e) t[e] += red[w][c][e];
@@ -303,25 +342,36 @@ __global__ void __launch_bounds__(kGThreads) graph_energy_kernel(GraphParams p) 
     }
 }
 
-// dynamic shared memory of the sweep kernel: amplitudes (72 B per mode) and record offsets (4 B per mode)
-static size_t graph_sweep_smem(int maxN) {
-    return (size_t)maxN * kGRS * sizeof(float2) + (size_t)(maxN + 1) * sizeof(int);
-}
+namespace {
+constexpr size_t kGraphSmemMax = 227 * 1024 - 8 * 1024;  // dynamic part (the static reduction table aside)
 
-cudaError_t graph_prepare(int maxN) {
-    const int sm = (int)graph_sweep_smem(maxN);  // 155 KB at N = 2048
-    cudaError_t e = cudaFuncSetAttribute(graph_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(graph_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+int graph_variant(int maxN, int max_deg) {
+    if (2 * max_deg <= kGWorkers) return kFew;
+    if (graph_smem(maxN, 2 * max_deg).total <= kGraphSmemMax) return kStage;
+    return kPlain;
+}
+}  // namespace
+
+cudaError_t graph_prepare(int maxN, int max_deg) {
+    const int var = graph_variant(maxN, max_deg);
+    const int sm = (int)graph_smem(maxN, var == kStage ? 2 * max_deg : 0).total;
+    cudaError_t e = cudaSuccess;
+    if (var == kFew) e = cudaFuncSetAttribute(graph_sweep_kernel<kFew>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    else if (var == kStage)
+        e = cudaFuncSetAttribute(graph_sweep_kernel<kStage>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    else e = cudaFuncSetAttribute(graph_sweep_kernel<kPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int se = maxN * kGRS * (int)sizeof(float2);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
     return e;
 }
 
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s) {
     if (n_groups <= 0) return cudaSuccess;
-    const size_t sm = graph_sweep_smem(p.maxN);
-    if (2 * p.max_deg <= kGWorkers) graph_sweep_kernel<true><<<n_groups, kGThreads, sm, s>>>(p);
-    else graph_sweep_kernel<false><<<n_groups, kGThreads, sm, s>>>(p);
+    const int var = graph_variant(p.maxN, p.max_deg);
+    const size_t sm = graph_smem(p.maxN, var == kStage ? 2 * p.max_deg : 0).total;
+    if (var == kFew) graph_sweep_kernel<kFew><<<n_groups, kGThreads, sm, s>>>(p);
+    else if (var == kStage) graph_sweep_kernel<kStage><<<n_groups, kGThreads, sm, s>>>(p);
+    else graph_sweep_kernel<kPlain><<<n_groups, kGThreads, sm, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -149,7 +149,7 @@ struct GraphParams {
 cudaError_t launch_wait_probe(Control *ctl, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s);
 cudaError_t launch_graph_energy(const GraphParams &p, int n_groups, cudaStream_t s);
-cudaError_t graph_prepare(int maxN);  // shared-memory limit of the graph kernels for N up to maxN
+cudaError_t graph_prepare(int maxN, int max_deg);  // shared-memory limits of the graph kernels (N <= maxN)
 
 struct PlainParams {
     const SampleDev *samples;
