@@ -189,3 +189,23 @@ def test_learned_global_moves_on_the_random_graph(prec):
         s = int(c) // (R * nT)
         ref = oracle.energy(N, graphs[s], Js[s], a1.reshape(-1, N)[c])
         assert abs(E1[c] - ref) <= 1e-13 * np.abs(Js[s]).sum(), (c, E1[c], ref)
+
+
+@pytest.mark.parametrize("N", [96, 128])
+def test_fp32_graph_variants_keep_energies_and_constraint(N):
+    """The FP32 group kernel stages an update's record lists in shared memory when they fit (N = 96: 132 KB)
+    and reads them from L2 otherwise (N = 128: the lists would need 235 KB); either way the running energies
+    stay the oracle's energies of the states and the constraint holds."""
+    R, nT = 2, 2
+    graphs, Js = _graphs([N], 1400 + N)
+    deg = np.bincount(graphs[0].ravel(), minlength=N).max()
+    assert (N * 72 + (N + 1) * 4 + 2 * deg * 20 <= 219 * 1024) == (N == 96)
+    temps = workload.geometric_ladder(0.5, 1.5, nT)
+    pt = pkg.PT([N], Js, temps, R, 23, precision="fp32", graphs=graphs, swap_every=2, measure_every=1,
+                resync_every=0)
+    pt.sweep(4)
+    a1, E1 = pt.state()
+    xs = _split(a1, [N], R, nT)
+    Eo = [oracle.energy(N, graphs[0], Js[0], x) for x in xs]
+    assert np.allclose(E1, Eo, rtol=1e-4, atol=1e-3), np.abs(np.asarray(E1) - Eo).max()
+    assert np.allclose([(np.abs(x) ** 4).sum() / len(x) for x in xs], 1.0, rtol=1e-4)
