@@ -340,6 +340,52 @@ def graph_leg(sweeps=64, plain_sweeps=4):
                                              "x 2 replicas, FP32 group kernels"}}
 
 
+def workloads_leg(sweeps=64):
+    """The other synthetic workloads at 1 GPU, each a PT run with its own swap (64), measurement (16) and
+    resync (64) schedule: chain-sweeps/s from CUDA events on the library's stream over `sweeps` sweeps after
+    2 warm-up sweeps, and the achieved fraction of the derived peak (FP32, or FP64 for the FP64 path) from
+    the same algorithmic flop count as the roofline of the main line.  The ragged batch runs the shape the
+    autotuner picks on it."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    Wall = workload.workloads()
+    fl_cache = {}
+    peak64 = 152 * 2 * 2 * 2070.0 * 1e6 / 1e12  # 2 FP64 FMA per SM per clock (nominal 1.25 TFLOP/s)
+    out = {}
+    for key, name, prec, tune in (("n16_fp64", "n16_fp64", "fp64", False), ("n64_batched_fp32", "n64_batched", "fp32", False),
+                                  ("n64_batched_fp64", "n64_batched", "fp64", False), ("ragged_fp32", "ragged", "fp32", True)):
+        W = Wall[name]
+        Js = [workload.couplings(n, len(pkg.enumerate_quads(n)), sd) for n, sd in zip(W.Ns, W.seeds)]
+        stream = torch.cuda.Stream()
+        pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 51, precision=prec, stream=stream, swap_every=64,
+                    measure_every=16, resync_every=64)
+        shape = pt.autotune() if tune else None
+        pt.sweep(2)
+        pt.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pt.sweep(sweeps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        per_chain = W.replicas * len(W.temps)
+        fl = 0.0
+        for n in W.Ns:
+            if n not in fl_cache:
+                fl_cache[n] = flops_per_chain_sweep(n)
+            fl += fl_cache[n] * per_chain * sweeps
+        peak = peak_fp32_tflops() if prec == "fp32" else peak64
+        achieved = fl / sec / 1e12
+        out[key] = {"value": pt.n_chains * sweeps / sec, "unit": "chain-sweeps/s", "precision": prec,
+                    "chains": pt.n_chains, "N": sorted(set(int(n) for n in W.Ns)), "sweeps": sweeps,
+                    "achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak,
+                    "peak_basis": "derived FP32 peak" if prec == "fp32" else "2 FP64 FMA/SM/clock x 152 SMs x 2070 MHz",
+                    "autotuned_shape": list(shape) if shape else None}
+        pt.close()
+    return out
+
+
 def ladder_leg():
     """App. A: specific heat on a ladder of fixed Delta T (N = 64 comb, 8 samples x 32 T [0.2,1.6] x 2
     replicas), the ladder T_i = T_{i-1}/(1 - 0.6/sqrt(C_V(T_i))), and the swap acceptance per neighbouring
@@ -452,6 +498,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal ESS comparison")
     ap.add_argument("--no-graph", action="store_true", help="skip the random-frequency graph leg")
     ap.add_argument("--no-ladder", action="store_true", help="skip the adaptive-ladder leg")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the leg of the other synthetic workloads")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     ap.add_argument("--profile-global", action="store_true",
@@ -510,6 +557,9 @@ def main():
     ladder = None
     if rank == 0 and world == 1 and not args.no_ladder:
         ladder = ladder_leg()
+    wl = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        wl = workloads_leg()
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -528,7 +578,8 @@ def main():
                                    "speedup_fp32": r["value"] / world / r["plain_rate"]},
                 "learned_vs_plain": learned,
                 "random_graph": graph,
-                "adaptive_ladder": ladder}
+                "adaptive_ladder": ladder,
+                "workloads": wl}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
