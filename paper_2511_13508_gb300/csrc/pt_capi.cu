@@ -866,18 +866,30 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     // ---- scheduling shape
     const int chains_ps = replicas * n_T;
     // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
-    // N >= 128: 8 chains x 11 warps; 48 <= N < 128: 32 x 7 when a sample has >= 32 chains; else 16 x 7
+    // N >= 128: 8 chains x 11 warps; 48 <= N < 128: the most chains per block (32, 16, 8) that still give
+    // about one group per SM (N = 64: 32 x 7 for 64 samples x 64 chains, 19.6M chain-sweeps/s, against
+    // 11.3M with 8 x 11; but 8 x 11 for 16 samples x 64 chains, 9.3k sweeps/s against 4.9k with 32 x 7, which
+    // leaves most SMs idle), 32 x 7 when none does; N < 48: 16 x 7
     int G = cfg.chains_per_block, ncw = 0;
     if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
     if (G == 0) {
         if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
         else if (c->maxN >= 128) G = 8;
-        else if (c->maxN >= 48 && chains_ps >= 32) G = 32;
-        else G = 16;
+        else if (c->maxN >= 48) {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                sms = 0;
+            for (int g : {32, 16, 8}) {
+                if (G == 0 && sms > 0 && (int64_t)S * ((chains_ps + g - 1) / g) >= (int64_t)sms * 4 / 5) G = g;
+            }
+            if (G == 0) G = chains_ps >= 32 ? 32 : 16;
+        } else {
+            G = 16;
+        }
         if (G > 8 && chains_ps <= 8) G = 8;
     }
     if (c->dbl) ncw = (G == 16) ? 3 : 7;
-    else ncw = (G == 8) ? (c->maxN >= 128 ? 11 : 7) : 7;
+    else ncw = (G == 8) ? (c->maxN >= 48 ? 11 : 7) : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !c->gfp32 && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;
