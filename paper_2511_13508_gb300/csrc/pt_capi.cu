@@ -869,11 +869,11 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     // N >= 128: 8 chains x 11 warps; 48 <= N < 128: the most chains per block (32, 16, 8) that still give
     // about one group per SM (N = 64: 32 x 7 for 64 samples x 64 chains, 19.6M chain-sweeps/s, against
     // 11.3M with 8 x 11; but 8 x 11 for 16 samples x 64 chains, 9.3k sweeps/s against 4.9k with 32 x 7, which
-    // leaves most SMs idle), 32 x 7 when none does; N < 48: 16 x 7
+    // leaves most SMs idle), 32 x 7 when none does; N < 48: 16 x 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3
     int G = cfg.chains_per_block, ncw = 0;
     if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
     if (G == 0) {
-        if (c->dbl) G = (c->maxN >= 64) ? 8 : 16;
+        if (c->dbl) G = (c->maxN >= 128) ? 8 : 16;  // FP64, N = 64, 64 samples: 16 x 3 685k, 8 x 7 521k
         else if (c->maxN >= 128) G = 8;
         else if (c->maxN >= 48) {
             int dev = 0, sms = 0;
