@@ -376,13 +376,14 @@ def test_accepted_global_moves_carry_the_energy_of_the_stored_state(prec):
         assert abs(E[c] - ref) <= 1e-13 * np.abs(J[s_]).sum(), (c, E[c], ref)
 
 
-@pytest.mark.parametrize("N,R,ncold,blocks", [(64, 4, 4, (0, 7)), (32, 8, 3, (2, 6)), (16, 16, 4, (0, 0))])
-def test_one_launch_sampler_draws_the_per_block_proposals(N, R, ncold, blocks):
+@pytest.mark.parametrize("N,S,R,nT,ncold,blocks", [(64, 2, 4, 4, 4, (0, 7)), (32, 2, 8, 4, 3, (2, 6)),
+                                                     (16, 2, 16, 4, 4, (0, 0)), (64, 16, 2, 32, 8, (0, 7))])
+def test_one_launch_sampler_draws_the_per_block_proposals(N, S, R, nT, ncold, blocks):
     """The autoregressive sampling in one launch (network weights on chip, draws written into the next pass's
     input in distributed shared memory) must draw exactly the proposals of the per-block launches: the same
     random streams and arithmetic, so after a series of global moves both ensembles hold bit-identical states,
-    energies and acceptance counts."""
-    S, nT = 2, 4
+    energies and acceptance counts.  The last case has the learned-proposal benchmark's shape (16 samples x
+    32 T x 2 replicas, the 8 coldest temperatures: 16 clusters of 4 blocks)."""
     temps = workload.geometric_ladder(0.5, 1.5, nT)
     J = [0.05 * j for j in _couplings([N] * S)]
     runs = []
