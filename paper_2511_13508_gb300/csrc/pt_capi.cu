@@ -1017,8 +1017,10 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         CK(cudaMemcpy(c->d_inc_off, hinc_off.data(), hinc_off.size() * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->d_inc, hinc.data(), hinc.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (c->gfp32) {
-            // incidence records: for each mode l and quadruplet q holding it, the other three modes in
-            // position order and (q << 2) | position of l, with J_q alongside
+            // incidence records: for each mode l and quadruplet q holding it, the other three modes A, B, C
+            // as row offsets of the kernel's amplitude table, ordered so that l's field term is
+            // J a_A a_B conj(a_C) (positions 0 and 3 are conjugated in the term; the field of a mode at
+            // position 1 or 2 is the conjugate), and the four positions packed in w; J_q alongside
             std::vector<int4> hrec(hinc.size());
             std::vector<float> hrecJ(hinc.size());
             for (int s = 0; s < S; ++s) {
@@ -1034,7 +1036,17 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
                             if (m4[m] == l) pos = m;
                             else if (n < 3) o[n++] = m4[m];
                         }
-                        hrec[sd.inc_off + e] = make_int4(o[0], o[1], o[2], (q << 2) | pos);
+                        // partner positions in ascending order (the positions other than pos), then the
+                        // order A, B, C: pos 0 -> (1, 2, 3); pos 1 -> (0, 3, 2); pos 2 -> (0, 3, 1); pos 3 -> (1, 2, 0)
+                        int op[3], n2 = 0;
+                        for (int m = 0; m < 4; ++m)
+                            if (m != pos) op[n2++] = m;
+                        const int perm[4][3] = {{0, 1, 2}, {0, 2, 1}, {0, 2, 1}, {1, 2, 0}};
+                        const int *pm = perm[pos];
+                        const int R = ptgb::kGraphRowStride;
+                        hrec[sd.inc_off + e] =
+                            make_int4(o[pm[0]] * R, o[pm[1]] * R, o[pm[2]] * R,
+                                      pos | (op[pm[0]] << 2) | (op[pm[1]] << 4) | (op[pm[2]] << 6));
                         hrecJ[sd.inc_off + e] = (float)hJq[sd.q_off + q];
                     }
             }

@@ -24,7 +24,8 @@ constexpr int kGG = 8;                      // chains per block
 constexpr int kGThreads = 1024;             // 32 warps
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGWorkers = kGThreads / kGG;  // 128
-constexpr int kGRS = kGG + 1;               // padded row stride of the amplitude table (float2)
+constexpr int kGRS = kGraphRowStride;       // padded row stride of the amplitude table (float2): kGG + 1
+static_assert(kGRS == kGG + 1, "row stride");
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -181,27 +182,23 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
                 const int r = onj ? oj + idx : ok + idx - nj;
                 const int4 R4 = kFewV ? R4f : (kStageV ? rec_s[idx] : __ldg(rec + r));
                 const float J = kFewV ? Jf : (kStageV ? recJ_s[idx] : __ldg(recJ + r));
-                const int pos = R4.w & 3;         // position of the record's own mode (j or k)
-                const int other = onj ? k : j;    // the other updated mode, possibly among the three
-                const int o[3] = {R4.x, R4.y, R4.z};
-                int po = -1;                      // index (0..2) of the other updated mode in o
+                const int pos = R4.w & 3;              // position of the record's own mode (j or k)
+                const int otherR = (onj ? k : j) * kGRS;  // the other updated mode, possibly among the three
+                const int o[3] = {R4.x, R4.y, R4.z};   // row offsets of A, B, C
+                int po = -1;                           // index (0..2) of the other updated mode among them
 #pragma unroll
-                for (int m = 0; m < 3; ++m) if (o[m] == other) po = m;
-                if (!onj && po >= 0) continue;    // holds both: counted once, from j's list
-                // positions of o[0..2]: the positions other than pos, ascending
-                int opos[3];
-#pragma unroll
-                for (int m = 0; m < 3; ++m) opos[m] = m + (m >= pos ? 1 : 0);
-                float2 f[3];
-#pragma unroll
-                for (int m = 0; m < 3; ++m) f[m] = fac(ga[o[m] * kGRS + c], opos[m]);
-                // field of the record's mode: J x (product of the other three), conjugated at positions 1, 2
-                float2 X = make_float2(J * f[0].x, J * f[0].y);
-                X = cmulf(cmulf(X, f[1]), f[2]);
-                if (pos == 1 || pos == 2) X.y = -X.y;
+                for (int m = 0; m < 3; ++m) if (o[m] == otherR) po = m;
+                if (!onj && po >= 0) continue;         // holds both: counted once, from j's list
+                const float2 fa = ga[o[0] + c], fb = ga[o[1] + c], fc = ga[o[2] + c];
+                // field of the record's mode: J a_A a_B conj(a_C)
+                const float2 ab = cmulf(fa, fb);
+                const float2 X = make_float2(J * (ab.x * fc.x + ab.y * fc.y), J * (ab.y * fc.x - ab.x * fc.y));
                 if (onj) { hj.x += X.x; hj.y += X.y; } else { hk.x += X.x; hk.y += X.y; }
                 if (po >= 0) {
-                    // the quadruplet holds j (this record) and k (o[po]): k's field and the cross term
+                    // the quadruplet holds j (this record) and k: k's field and the cross term, from the
+                    // positions of the factors (conjugated at positions 0 and 3)
+                    const int opos[3] = {(R4.w >> 2) & 3, (R4.w >> 4) & 3, (R4.w >> 6) & 3};
+                    const float2 f[3] = {fac(fa, opos[0]), fac(fb, opos[1]), fac(fc, opos[2])};
                     const float2 own = fac(ga[j * kGRS + c], pos);
                     const int pk = opos[po];
                     float2 Y = make_float2(J * own.x, J * own.y), Z = make_float2(J, 0.f);

@@ -119,6 +119,10 @@ cudaError_t launch_measure(const MeasureParams &p, cudaStream_t s);
 
 // Plain FP64 path: the paper's design restated (one block per chain, one thread per quadruplet term).
 // pt_graph.cu: FP32 sweep / energy on explicit interaction lists (one block per group of 8 chains)
+// Row stride (in float2) of the FP32 group kernels' amplitude table: 8 chains + 1 pad.  The incidence records
+// hold partner modes as row offsets (mode x this).
+constexpr int kGraphRowStride = 9;
+
 struct GraphParams {
     const SampleDev *samples;
     const GroupDev *groups;
@@ -126,7 +130,10 @@ struct GraphParams {
     const double *Jd;        // FP64 couplings (energy kernel)
     const int *inc_off;      // per sample mode: offsets into the incidence records (N+1, at mode_off)
     int max_deg;             // largest number of records of one mode, over all samples
-    const int4 *rec;         // incidence records per mode (at inc_off): other three modes, (q << 2) | position
+    // incidence records per mode (at inc_off): the other three modes A, B, C as row offsets (mode x
+    // kGraphRowStride), ordered so that the record's field term is J a_A a_B conj(a_C); w = position of the
+    // record's own mode | positions of A, B, C << 2, 4, 6
+    const int4 *rec;
     const float *recJ;       // coupling of each incidence record
     float2 *a;
     double *E;
