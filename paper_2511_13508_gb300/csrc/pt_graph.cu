@@ -177,24 +177,22 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
             float cr = 0.f;
             const int oj = inc_off[j], nj = inc_off[j + 1] - oj;
             const int ok = inc_off[k], nk = inc_off[k + 1] - ok;
-            for (int idx = worker; idx < nj + nk; idx += kGWorkers) {
-                const bool onj = idx < nj;
-                const int r = onj ? oj + idx : ok + idx - nj;
-                const int4 R4 = kFewV ? R4f : (kStageV ? rec_s[idx] : __ldg(rec + r));
-                const float J = kFewV ? Jf : (kStageV ? recJ_s[idx] : __ldg(recJ + r));
+            // one record of mode j (onj) or k: its field term, and for a quadruplet holding both (counted once,
+            // from j's list) k's term and the cross term
+            auto term = [&](const int4 R4, const float J, const bool onj) {
                 const int pos = R4.w & 3;              // position of the record's own mode (j or k)
                 const int otherR = (onj ? k : j) * kGRS;  // the other updated mode, possibly among the three
                 const int o[3] = {R4.x, R4.y, R4.z};   // row offsets of A, B, C
                 int po = -1;                           // index (0..2) of the other updated mode among them
 #pragma unroll
                 for (int m = 0; m < 3; ++m) if (o[m] == otherR) po = m;
-                if (!onj && po >= 0) continue;         // holds both: counted once, from j's list
+                if (!onj && po >= 0) return;
                 const float2 fa = ga[o[0] + c], fb = ga[o[1] + c], fc = ga[o[2] + c];
                 // field of the record's mode: J a_A a_B conj(a_C)
                 const float2 ab = cmulf(fa, fb);
                 const float2 X = make_float2(J * (ab.x * fc.x + ab.y * fc.y), J * (ab.y * fc.x - ab.x * fc.y));
                 if (onj) { hj.x += X.x; hj.y += X.y; } else { hk.x += X.x; hk.y += X.y; }
-                if (po >= 0) {
+                if (onj && po >= 0) {
                     // the quadruplet holds j (this record) and k: k's field and the cross term, from the
                     // positions of the factors (conjugated at positions 0 and 3)
                     const int opos[3] = {(R4.w >> 2) & 3, (R4.w >> 4) & 3, (R4.w >> 6) & 3};
@@ -211,6 +209,16 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
                     const float2 dxk = (pk == 0 || pk == 3) ? make_float2(P.dk.x, -P.dk.y) : P.dk;
                     cr += cmulf(Z, cmulf(dxj, dxk)).x;
                 }
+            };
+            if (kFewV) {  // at most one record per worker, prefetched
+                if (worker < nj + nk) term(R4f, Jf, worker < nj);
+            } else {      // j's list, then k's (the list a record comes from is then known at compile time)
+                for (int idx = worker; idx < nj; idx += kGWorkers)
+                    term(kStageV ? rec_s[idx] : __ldg(rec + oj + idx), kStageV ? recJ_s[idx] : __ldg(recJ + oj + idx),
+                         true);
+                for (int idx = worker; idx < nk; idx += kGWorkers)
+                    term(kStageV ? rec_s[nj + idx] : __ldg(rec + ok + idx),
+                         kStageV ? recJ_s[nj + idx] : __ldg(recJ + ok + idx), false);
             }
             // reduce over the 4 workers of the warp, then over the warps in a fixed order
             float v[5] = {hj.x, hj.y, hk.x, hk.y, cr};
