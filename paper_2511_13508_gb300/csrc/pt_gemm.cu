@@ -243,10 +243,12 @@ __global__ void __launch_bounds__(128, 2) gemm_bf16_tc_kernel(GemmParams p) {
 //    block, in the canonical layout with a K-group stride of Mp x 16 bytes.  The MMA reads 128 rows; rows
 //    >= Mp read whatever follows (each buffer is padded so that this stays inside the block's shared memory)
 //    and only produce accumulator lanes nobody reads.
-//  - After a hidden layer each block writes its BF16 column slice of relu(acc + b (+ C1[cond])) into the next
-//    activation buffer of all blocks of the cluster (distributed shared memory); a cluster barrier makes the
-//    writes visible before the next layer's MMAs.
+//  - After a hidden layer each block writes its BF16 column slice of relu(acc + b (+ C1[cond])) into its own
+//    next activation buffer (the slice is 8 contiguous K-groups) and one thread sends it to the three peers
+//    with shared-to-shared bulk copies that complete on the peer's exchange mbarrier; a block starts the next
+//    layer once its barrier has counted the three slices.
 //  - 8 warps read the accumulator back: warp w takes TMEM lanes 32 (w % 4).. and half of the slice's columns.
+//  - Biases and the C1 columns of the block are staged in shared memory at the start.
 namespace {
 
 constexpr int kMlpCL = 4;         // blocks per sample (cluster size)
