@@ -52,6 +52,7 @@ def lib() -> ctypes.CDLL:
         L.or_field.argtypes = [ctypes.c_int, c_i64, vp, vp, vp, ctypes.c_int, vp]
         L.or_delta_h.argtypes = [ctypes.c_int, c_i64, vp, vp, c_d, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.or_delta_h.restype = c_d
+        L.or_cross_terms.argtypes = [ctypes.c_int, c_i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.or_pair.argtypes = [c_u64, c_u32, c_u32, c_u32, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
         L.or_propose.argtypes = [c_u64, c_u32, c_u32, c_u32, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.or_propose.restype = c_d
@@ -132,6 +133,15 @@ def delta_h(N, quads, J, a, j, k, aj_new, ak_new, cc=2.0) -> float:
     a = np.ascontiguousarray(a, dtype=np.complex128)
     aj = np.array([aj_new.real, aj_new.imag]); ak = np.array([ak_new.real, ak_new.imag])
     return lib().or_delta_h(int(N), len(J), _p(quads), _p(J), float(cc), _p(a), int(j), int(k), _p(aj), _p(ak))
+
+
+def cross_terms(N, quads, J, a, j, k):
+    """(B_jk, A_jk): the bilinear part of the pair-move energy change, -cc Re[conj(dj) dk B + conj(dj) conj(dk) A]."""
+    quads = np.ascontiguousarray(quads, dtype=np.int32); J = np.ascontiguousarray(J, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    B = np.zeros(2); A = np.zeros(2)
+    lib().or_cross_terms(int(N), len(J), _p(quads), _p(J), _p(a), int(j), int(k), _p(B), _p(A))
+    return complex(B[0], B[1]), complex(A[0], A[1])
 
 
 def pair(seed, sample, sweep, update, N):

@@ -224,6 +224,34 @@ double or_delta_h(int N, int64_t nq, const int32_t *abcd, const double *J, doubl
     return delta_h_core(abcd, J, cc, a, j, k, aj_new, ak_new, NULL, 0, NULL, 0, nq);
 }
 
+/* The bilinear (j,k) part of the pair-move energy change (reading R5), split by the conjugation of the two
+ * increments: with a_j += dj, a_k += dk, the quadruplets holding both j and k change H by
+ *     -cc Re[ conj(dj) dk B + conj(dj) conj(dk) A ].
+ * For each such quadruplet let X = J_q times the factors of its other two positions (conjugated at
+ * positions 0 and 3).  Its term X x_j x_k, with x = conj(d) at positions 0, 3 and x = d at 1, 2, adds
+ * X to B (j conjugated, k plain), conj(X) to B (j plain, k conjugated), X to A (both conjugated) or
+ * conj(X) to A (both plain), since Re(z) = Re(conj(z)).  On the comb, B = sum J conj(a_m) a_y over
+ * quadruplets {j, m | k, y} with j+m = k+y and A = sum J a_x a_y over quadruplets {j, k | x, y}. */
+void or_cross_terms(int N, int64_t nq, const int32_t *abcd, const double *J, const double *a, int j, int k,
+                    double B[2], double A[2]) {
+    (void)N;
+    cplx Bs = {0.0, 0.0}, As = {0.0, 0.0};
+    for (int64_t q = 0; q < nq; ++q) {
+        const int32_t *Q = abcd + 4 * q;
+        int pj = -1, pk = -1;
+        for (int p = 0; p < 4; ++p) { if (Q[p] == j) pj = p; if (Q[p] == k) pk = p; }
+        if (pj < 0 || pk < 0) continue;
+        cplx X = {J[q], 0.0};
+        for (int p = 0; p < 4; ++p) if (p != pj && p != pk) X = cmul(X, xfactor(a, Q, p));
+        const int cj = (pj == 0 || pj == 3), ck = (pk == 0 || pk == 3);
+        const cplx add = cj ? X : cconj(X); /* the four cases above: X when j is conjugated, else conj(X) */
+        if (cj == ck) { As.re += add.re; As.im += add.im; }
+        else { Bs.re += add.re; Bs.im += add.im; }
+    }
+    B[0] = Bs.re; B[1] = Bs.im;
+    A[0] = As.re; A[1] = As.im;
+}
+
 /* ---------------------------------------------------------------- random draws */
 /* Pair choice (reading R3): j = floor(w0 N / 2^32), k = (j + 1 + floor(w1 (N-1) / 2^32)) mod N. */
 void or_pair(uint64_t seed, uint32_t sample, uint32_t sweep, uint32_t update, int N, int *j, int *k) {

@@ -150,6 +150,43 @@ def test_delta_h_matches_full_recompute(N):
     assert worst < 1e-11
 
 
+@pytest.mark.parametrize("N", [4, 7, 10, 16, 24])
+def test_cross_terms_complete_the_pair_change(N):
+    """H is multilinear in the factors of every quadruplet, so for a_j += dj, a_k += dk the change is exactly
+    -2 Re[conj(dj) h_j + conj(dk) h_k + conj(dj) dk B + conj(dj) conj(dk) A]: full recompute for several
+    independent (dj, dk) per pair determines B and A, so a swapped, conjugated or dropped term fails."""
+    rng = np.random.default_rng(300 + N)
+    q = oracle.enumerate_quads(N); J = rng.standard_normal(len(q)) / N
+    a = rand_state(N, rng, on_constraint=False)
+    E = oracle.energy(N, q, J, a)
+    pairs = [(0, N - 1), (N - 1, 0), (0, 1), (1, 0), (N // 2 - 1, N // 2)] + \
+        [tuple(rng.choice(N, 2, replace=False)) for _ in range(6)]
+    for j, k in pairs:
+        hj, hk = oracle.field(N, q, J, a, j), oracle.field(N, q, J, a, k)
+        B, A = oracle.cross_terms(N, q, J, a, j, k)
+        for _ in range(4):
+            dj, dk = complex(*rng.standard_normal(2)), complex(*rng.standard_normal(2))
+            b = a.copy(); b[j] += dj; b[k] += dk
+            full = oracle.energy(N, q, J, b) - E
+            dec = -2.0 * (np.conj(dj) * hj + np.conj(dk) * hk + np.conj(dj) * dk * B + np.conj(dj) * np.conj(dk) * A).real
+            assert dec == pytest.approx(full, rel=1e-10, abs=1e-12), (j, k)
+
+
+def test_cross_terms_single_quadruplet_closed_form():
+    """N = 4, quadruplet (0,1,2,3), term J conj(a0) a1 a2 conj(a3): both modes of one pair give A = J times the
+    other pair's plain product; modes of different pairs give B = J conj(m) y with j+m = k+y."""
+    rng = np.random.default_rng(5)
+    q = oracle.enumerate_quads(4); J = np.array([0.7])
+    a = rand_state(4, rng, on_constraint=False)
+    c = np.conj
+    cases = {(0, 3): (0.0, 0.7 * a[1] * a[2]), (1, 2): (0.0, 0.7 * a[0] * a[3]),
+             (0, 1): (0.7 * c(a[3]) * a[2], 0.0), (0, 2): (0.7 * c(a[3]) * a[1], 0.0),
+             (1, 0): (0.7 * c(a[2]) * a[3], 0.0), (2, 3): (0.7 * c(a[1]) * a[0], 0.0)}
+    for (j, k), (Bref, Aref) in cases.items():
+        B, A = oracle.cross_terms(4, q, J, a, j, k)
+        assert abs(B - Bref) < 1e-14 and abs(A - Aref) < 1e-14, (j, k, B, Bref, A, Aref)
+
+
 # ------------------------------------------------------------------------------------ move
 def test_pair_draw_distribution():
     """j uniform on [0,N), k uniform on the other N-1 modes (chi-square on the joint counts)."""
