@@ -183,6 +183,21 @@ int pt_energy(pt_ctx *ctx, double *E);
  * for a_j += dj, a_k += dk.  Not available for PT_PREC_FP64_PLAIN (PT_EUNSUPPORTED). */
 int pt_fields(pt_ctx *ctx, int sample, int j, int k, double *out);
 
+/* Update trace of the sweep kernel itself (Sec. III.A.1 pair move, Sec. III.A.3 parallel Delta E): runs
+ * the next sweep exactly as pt_sweep(ctx, 1) would (same kernel, block shape and graph, then the schedule
+ * due after it) while the production kernel records pair update `update` (0 <= update < N/2) of that
+ * sweep for every chain of every sample with N[s]/2 > update.  Outputs, canonical (s, r, t) order:
+ *   rec [n_chains][PT_TRACE_REC] doubles: j, k, h_j (re, im), h_k (re, im), B_jk (re, im), A_jk (re, im)
+ *       as the kernel reduced them (definitions as in pt_fields), the proposed a_j', a_k' (re, im each),
+ *       the Metropolis uniform U, the kernel's Delta H, accepted (0/1), beta, the running energy before the
+ *       update, and 1.0 for a written record (0.0 everywhere for chains that were not traced);
+ *   a   optional (NULL = not wanted), state layout of pt_get_state: every traced chain's amplitudes just
+ *       before the update, in the kernel's precision widened to double.
+ * Caller-owned host buffers; the call synchronises the context's stream.  PT_EINVAL for an update outside
+ * [0, max N/2); PT_EUNSUPPORTED for the quadruplet-list paths (PT_PREC_FP64_PLAIN, pt_create_graph). */
+#define PT_TRACE_REC 20
+int pt_trace_update(pt_ctx *ctx, int update, double *rec, double *a);
+
 /* Checkpoint.  pt_save with buf == NULL stores the needed size in *len; otherwise writes *len bytes
  * (PT_EINVAL if *len is too small).  pt_load restores a checkpoint of a context created with the
  * same arguments (PT_ESTATE otherwise); resuming is bit-identical to an uninterrupted run. */
@@ -302,12 +317,28 @@ int pt_gemm_bf16(int batch, int M, int N, int K, const void *A, const void *B, f
  * routine): its working table is a static device array of 20336 int4 (325 KB) that every GPU loading
  * the library holds until exit.  Every call rewrites the part of the table it uses, so a call never
  * sees stale contents, but all calls share the one table: calls that overlap on the GPU (other streams
- * or threads, same device) race and must be serialised by the caller.  The first call on a device
- * looks up the table's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Errors: PT_EINVAL (arguments), PT_ECUDA (no device, lookup or
- * launch failure); the message is in pt_last_error(NULL). */
+ * or threads, same device) race and must be serialised by the caller.  The table's device address is
+ * only valid in the CUDA context in which it was looked up (cudaGetSymbolAddress): a call made while
+ * `stream` is not capturing looks it up again in the context current on the calling thread and records it
+ * for that context; a call made during stream capture uses the address an earlier call recorded for the
+ * current context, so make the first call in each context before any stream capture (PT_EINVAL
+ * otherwise).  Errors: PT_EINVAL (arguments), PT_ECUDA (a CUDA error left pending by earlier work on the
+ * thread, no context, lookup or launch failure, each with the CUDA error string); the message is in
+ * pt_last_error(NULL). */
 int pt_energy_fp64_static(int N, int n_chains, const double *J, const double *a, double *E, double cc,
                           void *stream);
+
+/* ---- Measurement probe (not part of the paper's method).  The sweep is bound by FP32 arithmetic, so its
+ * roofline is the FP32 fused multiply-add throughput of the GPU it runs on, measured here instead of derived
+ * from unit counts and a nominal clock.  Launches `blocks` x `threads` threads, each running 8 independent
+ * fused multiply-add chains for `iters` iterations: packed != 0 issues them as paired FP32 FMAs (two per
+ * instruction), packed == 0 as scalar FMAs; either way 32 flops per thread and iteration, so one launch
+ * does blocks * threads * iters * 32 flops.  sink: caller-owned device buffer of blocks * threads floats
+ * (written only in a case that cannot occur; it keeps the arithmetic alive).  Asynchronous on `stream`
+ * (cudaStream_t, NULL = legacy default stream): time it with events on that stream.  Errors: PT_EINVAL
+ * (threads not a multiple of 32 in [32, 1024], blocks or iters < 1, NULL sink), PT_ECUDA (launch);
+ * message in pt_last_error(NULL). */
+int pt_fma_probe(int packed, int blocks, int threads, int iters, float *sink, void *stream);
 
 #ifdef __cplusplus
 }

@@ -15,10 +15,11 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["build", "lib", "PT", "enumerate_quads", "fmc_graph", "PREC", "PTError", "NSTAT", "NQSTAT", "QBINS"]
+__all__ = ["build", "lib", "PT", "enumerate_quads", "fma_probe", "fmc_graph", "PREC", "PTError", "NSTAT", "NQSTAT", "QBINS", "TRACE_REC"]
 
 PREC = {"fp32": 0, "fp64": 1, "fp64_plain": 2}
 NSTAT, NQSTAT, QBINS = 7, 5, 201
+TRACE_REC = 20  # doubles per chain of pt_trace_update
 _ERRORS = {-1: "PT_EINVAL", -2: "PT_ENOMEM", -3: "PT_ECUDA", -4: "PT_ETIMEOUT", -5: "PT_ENAN",
            -6: "PT_ESTATE", -7: "PT_EUNSUPPORTED"}
 
@@ -47,10 +48,10 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "pt_swap", "pt_resync",
            "pt_measure_now", "pt_measure", "pt_reset_observables", "pt_get_state", "pt_set_state", "pt_energy",
-           "pt_fields", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
+           "pt_fields", "pt_trace_update", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
            "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_set_global_sampler", "pt_gemm_bf16",
-           "pt_energy_fp64_static", "pt_fmc_graph", "pt_create_graph", "pt_check_wait"]
+           "pt_energy_fp64_static", "pt_fma_probe", "pt_fmc_graph", "pt_create_graph", "pt_check_wait"]
 
 _lib = None
 
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
         L.pt_set_state.argtypes = [vp, vp]
         L.pt_energy.argtypes = [vp, vp]
         L.pt_fields.argtypes = [vp, i, i, i, vp]
+        L.pt_trace_update.argtypes = [vp, i, vp, vp]
         L.pt_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.pt_load.argtypes = [vp, vp, ctypes.c_size_t]
         L.pt_counters.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -100,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.pt_learn_eval.argtypes = [vp, vp, vp, i, vp, vp, vp]
         L.pt_gemm_bf16.argtypes = [i, i, i, i, vp, vp, vp, vp]
         L.pt_energy_fp64_static.argtypes = [i, i, vp, vp, vp, d, vp]
+        L.pt_fma_probe.argtypes = [i, i, i, i, vp, vp]
         L.pt_last_error.argtypes = [vp]; L.pt_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -120,6 +123,11 @@ def fmc_graph(omega, gamma=None) -> np.ndarray:
     out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
     _check(None, lib().pt_fmc_graph(N, _p(omega), g, _p(out), ctypes.byref(n)))
     return out[: n.value]
+
+
+def fma_probe(packed, blocks, threads, iters, sink_ptr, stream_ptr):
+    """Launches the FP32 FMA-pipe probe (pt_fma_probe): blocks * threads * iters * 32 flops on the stream."""
+    _check(None, lib().pt_fma_probe(int(packed), int(blocks), int(threads), int(iters), sink_ptr, stream_ptr))
 
 
 def enumerate_quads(N: int) -> np.ndarray:
@@ -272,6 +280,15 @@ class PT:
         out = np.zeros(self.R * self.nT * 8)
         self._c(lib().pt_fields(self._h, int(sample), int(j), int(k), _p(out)))
         return out.view(np.complex128).reshape(self.R * self.nT, 4)
+
+    def trace_update(self, update):
+        """Runs the next sweep with pair update `update` of the sweep kernel traced (pt_trace_update).
+        Returns (rec [n_chains, TRACE_REC] float64, state before the update [sum_s N_s R nT] complex128),
+        canonical (s, r, t) order; rec[:, 19] == 1 marks the traced chains."""
+        rec = np.zeros((self.n_chains, TRACE_REC))
+        a = np.zeros(int(self.Ns.astype(np.int64).sum()) * self.R * self.nT, np.complex128)
+        self._c(lib().pt_trace_update(self._h, int(update), _p(rec), _p(a)))
+        return rec, a
 
     def save(self) -> bytes:
         n = ctypes.c_size_t()

@@ -199,6 +199,7 @@ struct pt_ctx {
     unsigned long long *d_mc_acc = nullptr, *d_mc_att = nullptr, *d_mcT_acc = nullptr, *d_mcT_att = nullptr;
     unsigned long long *d_swap_acc = nullptr, *d_swap_att = nullptr, *d_qhist = nullptr;
     double *d_stat = nullptr, *d_qstat = nullptr, *d_fields = nullptr;
+    double *d_trace = nullptr;  // update trace of the sweep kernel (blocked-store paths)
     Control *d_ctl = nullptr;
     void *d_snap_a = nullptr;
     double *d_snap_E = nullptr;
@@ -367,7 +368,7 @@ int run_sweeps(pt_ctx *c, int seg) {
     p.R = c->R; p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
     p.progress = c->d_progress; p.n_sweeps = seg; p.sweeps_per_unit = std::min(c->spu, seg);
     p.measure_every = c->cfg.measure_every; p.snap_a = c->d_snap_a; p.snap_E = c->d_snap_E;
-    p.n_snap_max = c->n_snap_max; p.a_total = c->a_total; p.n_chains = c->n_chains;
+    p.n_snap_max = c->n_snap_max; p.a_total = c->a_total; p.n_chains = c->n_chains; p.trace = c->d_trace;
     const int units = ((seg + p.sweeps_per_unit - 1) / p.sweeps_per_unit) * p.n_groups;
     const int grid = std::max(1, std::min(c->grid, units));
     CK(launch_sweep(c->dbl, c->G, c->ncw, p, grid, c->stream));
@@ -967,6 +968,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     RC(dalloc(c, &c->d_stat, (size_t)S * n_T * PT_NSTAT));
     RC(dalloc(c, &c->d_qstat, (size_t)S * n_T * PT_NQSTAT));
     RC(dalloc(c, &c->d_fields, (size_t)chains_ps * 8));
+    if (!c->plain && !c->gfp32) RC(dalloc(c, &c->d_trace, (size_t)c->n_chains * kTraceRec + (size_t)c->a_total * 2));
     RC(dalloc(c, &c->d_ctl, 1));
 
     // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
@@ -1329,6 +1331,30 @@ int pt_fields(pt_ctx *c, int sample, int j, int k, double *out) {
         const int dst = canon[c0 + i] - c0;
         for (int e2 = 0; e2 < 8; ++e2) out[(size_t)dst * 8 + e2] = h[(size_t)i * 8 + e2];
     }
+    return PT_OK;
+}
+
+int pt_trace_update(pt_ctx *c, int update, double *rec, double *a) {
+    if (!c || !rec) return fail(c, PT_EINVAL, "pt_trace_update: NULL argument");
+    if (!c->d_trace) return fail(c, PT_EUNSUPPORTED, "pt_trace_update: not available for the quadruplet-list paths");
+    if (update < 0 || update >= c->maxN / 2) return fail(c, PT_EINVAL, "pt_trace_update: update must be in [0, maxN/2)");
+    int rc = watchdog_sync(c);
+    if (rc != PT_OK) return rc;
+    const size_t nrec = (size_t)c->n_chains * kTraceRec, bytes = (nrec + (size_t)c->a_total * 2) * sizeof(double);
+    CK(cudaMemsetAsync(c->d_trace, 0, bytes, c->stream));
+    // arm the trace for the next sweep (its absolute index + 1), run it with its schedule, disarm
+    struct { long long at; int u, pad; } on{c->sweeps_done + 1, update, 0}, off{0, -1, 0};
+    static_assert(sizeof(on) == 16, "trace words");
+    CK(cudaMemcpyAsync(&c->d_ctl->trace_at, &on, sizeof(on), cudaMemcpyHostToDevice, c->stream));
+    rc = pt_sweep(c, 1);
+    const cudaError_t e = cudaMemcpyAsync(&c->d_ctl->trace_at, &off, sizeof(off), cudaMemcpyHostToDevice, c->stream);
+    if (rc != PT_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(c, e, "pt_trace_update: disarm");
+    if ((rc = watchdog_sync(c)) != PT_OK) return rc;
+    std::vector<double> h(nrec + (size_t)c->a_total * 2);
+    CK(cudaMemcpy(h.data(), c->d_trace, bytes, cudaMemcpyDeviceToHost));
+    std::memcpy(rec, h.data(), nrec * sizeof(double));
+    if (a) std::memcpy(a, h.data() + nrec, (size_t)c->a_total * 2 * sizeof(double));
     return PT_OK;
 }
 

@@ -113,7 +113,15 @@ struct Control {
     long long sweep_base;   // sweeps done before the current sweep launch
     long long swap_passes;  // swap passes done
     long long global_rounds;  // learned global-move rounds done
+    long long trace_at;     // update trace: absolute sweep index + 1 of the traced sweep (0 = off)
+    int trace_update;       // update trace: pair update of that sweep
+    int trace_pad;
 };
+
+// One record of the update trace (doubles per chain, canonical chain order): the pair, the reduced sums
+// h_j, h_k, B_jk, A_jk, the proposal, the uniform, Delta H, the decision, beta, the running energy before
+// the update and a written flag.
+constexpr int kTraceRec = 20;
 
 constexpr int kErrTimeout = 1, kErrNaN = 2, kErrBadArg = 3;
 constexpr unsigned long long kWaitNs = 10000000000ull;  // bounded waits give up after 10 s of wall time

@@ -33,6 +33,9 @@ struct SweepParams {
     int n_snap_max;
     int64_t a_total;            // complex numbers in one full state
     int n_chains;
+    // update trace (armed by Control::trace_at / trace_update): [n_chains][kTraceRec] records, then the
+    // pre-update states [a_total] as double complex, both in canonical (sample, replica, temperature) order
+    double *trace;
 };
 
 struct FieldsParams {

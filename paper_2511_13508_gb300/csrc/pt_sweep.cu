@@ -464,6 +464,27 @@ __device__ __forceinline__ real delta_h(const Proposal<real> &P, const Partials<
     return -cc * (t1.x + t2.x + t3.x + t4.x);
 }
 
+// Update trace: one chain's record of the traced update and its state before the update (modes j and k from
+// the proposal's old amplitudes: the other warps may already have written the new ones).
+template <typename real, int RS>
+__device__ __noinline__ void trace_write(double *trace, int n_chains, int64_t a_off, int chain0, int N, uint32_t id,
+                                         int j, int k, Partials<real> f, Proposal<real> P, real dH, bool acc,
+                                         real beta, double E, const typename vec2<real>::type *as, int c) {
+    using V = typename vec2<real>::type;
+    double *rec = trace + (int64_t)id * kTraceRec;
+    const double v[kTraceRec] = {(double)j, (double)k, (double)f.hj.x, (double)f.hj.y, (double)f.hk.x,
+                                 (double)f.hk.y, (double)f.B.x, (double)f.B.y, (double)f.A.x, (double)f.A.y,
+                                 (double)P.nj.x, (double)P.nj.y, (double)P.nk.x, (double)P.nk.y, (double)P.U,
+                                 (double)dH, acc ? 1.0 : 0.0, (double)beta, E, 1.0};
+    for (int e = 0; e < kTraceRec; ++e) rec[e] = v[e];
+    double2 *st = reinterpret_cast<double2 *>(trace + (int64_t)n_chains * kTraceRec) + a_off +
+                  (int64_t)(id - (uint32_t)chain0) * N;
+    for (int x = 0; x < N; ++x) {
+        const V a = (x == j) ? P.aj : (x == k) ? P.ak : as[(x + APAD) * RS + c];
+        st[x] = make_double2((double)a.x, (double)a.y);
+    }
+}
+
 __device__ __forceinline__ bool metropolis_accept(float dH, float beta, float U) {
     return dH <= 0.0f || U < expf(-beta * dH);
 }
@@ -686,6 +707,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             // ---------------- consumer warps
             const int *mode_blk = prm.mode_blk + sd.mode_off;
             const uint32_t *binfo = prm.blkinfo + sd.blk_off;
+            // update trace: absolute sweep + 1 and update to record (0 = none)
+            const long long tr_at = prm.trace ? prm.ctl->trace_at : 0ll;
+            const int tr_u = prm.trace ? prm.ctl->trace_update : -1;
             const bool gatherB = kGatherB<real, G> && N >= kGatherBMinN;
             const real cc = (real)prm.cc;
             for (int sw = sw0; sw < sw1; ++sw) {
@@ -800,6 +824,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             const Proposal<real> P = Pp[c];
                             const real dH = delta_h<real>(P, f, cc);
                             const bool acc = (c < gr.count) && metropolis_accept(dH, cBeta[c], P.U);
+                            if (tr_at == sweep_base + sw + 1 && u == tr_u && warp == 0 && c < gr.count)
+                                trace_write<real, RS>(prm.trace, prm.n_chains, sd.a_off, sd.chain0, N, cId[c], j, k, f, P, dH, acc,
+                                                      cBeta[c], cE[c], as, c);
                             if (acc) {
                                 as[(j + APAD) * RS + c] = P.nj;
                                 as[(k + APAD) * RS + c] = P.nk;
