@@ -9,9 +9,12 @@
 //
 // The kernel is a variant of the plain FP64 energy kernel (one thread block per chain, one thread
 // per quadruplet term, shared-memory tree reduction), reading its quadruplet table from that array.
+#include <cuda.h>
+
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/pt.h"
 
@@ -24,14 +27,38 @@ namespace {
 constexpr int kStaticMaxN = 64;           // largest mode count the table holds
 constexpr int kStaticMaxQuads = 20336;    // quadruplets of the 64-mode comb
 constexpr int kStaticThreads = 256;
-constexpr int kMaxDevices = 64;
 
 // Working table shared by every call on a device; it keeps the last call's contents.
 static __device__ __align__(256) int4 g_static_quads[kStaticMaxQuads];
 
-// Host copies of the table's device address, one per device, set on the first call on that device.
-void *g_static_ptr[kMaxDevices] = {nullptr};
+// The table's device address belongs to the CUDA context in which it was looked up: one entry per context
+// (a plug-in host may run its own driver-API context next to the runtime's primary context).
+struct TableAddr {
+    CUcontext ctx;
+    void *table;
+};
+std::vector<TableAddr> g_static_tables;
 std::mutex g_static_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+std::once_flag g_ctx_once;
+
+// The context current on this thread (nullptr if none), through the driver entry point the runtime hands out
+// (no link-time dependence on the driver library).
+bool current_context(CUcontext *ctx) {
+    std::call_once(g_ctx_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+        else
+            (void)cudaGetLastError();
+    });
+    *ctx = nullptr;
+    return g_ctx_get_current && g_ctx_get_current(ctx) == CUDA_SUCCESS;
+}
 
 // One thread per first index a: writes every a<b<c<d with a+d = b+c, in lexicographic (a,b,c) order,
 // at the canonical position (the count of quadruplets with a smaller first index comes first).
@@ -80,9 +107,45 @@ __global__ void __launch_bounds__(kStaticThreads) static_energy_kernel(const int
     if (threadIdx.x == 0) E[blockIdx.x] = -cc * buf[0];
 }
 
-int static_fail(int code, const char *msg) {
-    ptgb::set_global_error(msg);
+int static_fail(int code, const std::string &msg) {
+    ptgb::set_global_error(msg.c_str());
     return code;
+}
+
+// Device address of the table in the current context.  Looked up with cudaGetSymbolAddress on every call
+// made while the stream is not capturing (the address is then always the current context's, even after a
+// device reset); a call made during stream capture takes the address an earlier call recorded for the
+// current context.
+int table_address(cudaStream_t s, void **table) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        return static_fail(PT_ECUDA, std::string("pt_energy_fp64_static: cannot query the stream: ") + cudaGetErrorString(e));
+    }
+    CUcontext ctx = nullptr;
+    if (!current_context(&ctx))
+        return static_fail(PT_ECUDA, "pt_energy_fp64_static: cannot read the current CUDA context");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (cap == cudaStreamCaptureStatusNone || !ctx) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_quads);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return static_fail(PT_ECUDA, std::string("pt_energy_fp64_static: cudaGetSymbolAddress failed: ") +
+                                             cudaGetErrorString(e));
+        }
+        if (!ctx && (!current_context(&ctx) || !ctx))  // the lookup above made the primary context current
+            return static_fail(PT_ECUDA, "pt_energy_fp64_static: no current CUDA context");
+        for (auto &t : g_static_tables)
+            if (t.ctx == ctx) { t.table = p; *table = p; return PT_OK; }
+        g_static_tables.push_back({ctx, p});
+        *table = p;
+        return PT_OK;
+    }
+    for (auto &t : g_static_tables)
+        if (t.ctx == ctx) { *table = t.table; return PT_OK; }
+    return static_fail(PT_EINVAL, "pt_energy_fp64_static: the first call in a CUDA context must come before any "
+                                  "stream capture (it looks up the static table's address)");
 }
 
 }  // namespace
@@ -94,37 +157,27 @@ extern "C" int pt_energy_fp64_static(int N, int n_chains, const double *J, const
     if (n_chains < 0 || (n_chains > 0 && (!J || !a || !E)))
         return static_fail(PT_EINVAL, "pt_energy_fp64_static: need n_chains >= 0 and device pointers J, a, E");
     if (n_chains == 0) return PT_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        (void)cudaGetLastError();
-        return static_fail(PT_ECUDA, "pt_energy_fp64_static: no current CUDA device");
-    }
+    // an error left pending by earlier work on this thread is reported as such, not as this call's failure
+    const cudaError_t pre = cudaGetLastError();
+    if (pre != cudaSuccess)
+        return static_fail(PT_ECUDA, std::string("pt_energy_fp64_static: CUDA error pending from earlier work: ") +
+                                         cudaGetErrorString(pre));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     void *table = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_static_mutex);
-        if (!g_static_ptr[dev]) {
-            void *p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_static_quads);
-            if (e != cudaSuccess || !p) {
-                (void)cudaGetLastError();
-                return static_fail(PT_ECUDA, "pt_energy_fp64_static: cudaGetSymbolAddress failed");
-            }
-            g_static_ptr[dev] = p;
-        }
-        table = g_static_ptr[dev];
-    }
+    const int rc = table_address(s, &table);
+    if (rc != PT_OK) return rc;
     int64_t nq = 0;
     for (int aa = 0; aa < N; ++aa)
         for (int b = aa + 1; b < N; ++b) {
             const int cnt = N - 1 - 2 * b + aa;
             if (cnt > 0) nq += cnt;
         }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int4 *quads = reinterpret_cast<int4 *>(table);
     static_fill_quads<<<1, kStaticMaxN, 0, s>>>(quads, N);
     static_energy_kernel<<<n_chains, kStaticThreads, 0, s>>>(quads, nq, J, reinterpret_cast<const double2 *>(a), N,
                                                              cc, E);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return static_fail(PT_ECUDA, "pt_energy_fp64_static: kernel launch failed");
+    if (e != cudaSuccess)
+        return static_fail(PT_ECUDA, std::string("pt_energy_fp64_static: kernel launch failed: ") + cudaGetErrorString(e));
     return PT_OK;
 }
