@@ -516,7 +516,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
            "samples_per_gpu": 16, "temps": 48, "replicas": 2, "N": N_MODES, "step": "64 sweeps + resync + "
-           "4 measurements + swap pass", "l2": "inputs larger than L2 (352 MB coupling store)"}
+           "4 measurements + swap pass", "l2": "inputs larger than L2 (398 MB blocked coupling store: 16 x 24.9 MB)"}
 
     if args.impl == "reference":
         if rank != 0:
