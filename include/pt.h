@@ -328,6 +328,22 @@ int pt_gemm_bf16(int batch, int M, int N, int K, const void *A, const void *B, f
 int pt_energy_fp64_static(int N, int n_chains, const double *J, const double *a, double *E, double cc,
                           void *stream);
 
+/* Incidence records of the FP32 quadruplet-list kernels (the sweep of pt_create_graph contexts), built on the
+ * host exactly as pt_create_graph builds them, for inspection and tests; no device work.  For a list of nq
+ * quadruplets of N modes (term order: the term of quadruplet (q0, q1, q2, q3) is J conj(a_q0) a_q1 a_q2
+ * conj(a_q3), Sec. II.C with Eq. (4)):
+ *   offsets [N+1]    records of mode l are rec[offsets[l] .. offsets[l+1]), one per quadruplet holding l, in
+ *                    list order;
+ *   rec [4 nq][4]    int32 (A, B, C, w): the three other modes as row offsets mode * 9 of the kernels'
+ *                    amplitude table, ordered so that the record's contribution to the local field of l
+ *                    (Sec. III.A.3, H = -cc Re(conj(a_l) h_l) + terms without l) is J a_A a_B conj(a_C);
+ *                    w = position of l | positions of A, B, C << 2, 4, 6;
+ *   recJ [4 nq]      J of the record's quadruplet in FP32.
+ * Caller-owned host buffers.  PT_EINVAL for N outside [4, 2048], nq < 0 or above 2^28, a mode index out of
+ * range or a NULL buffer. */
+int pt_graph_records(int N, int64_t nq, const int32_t *quads, const double *J, int32_t *offsets, int32_t *rec,
+                     float *recJ);
+
 /* ---- Measurement probe (not part of the paper's method).  The sweep is bound by FP32 arithmetic, so its
  * roofline is the FP32 fused multiply-add throughput of the GPU it runs on, measured here instead of derived
  * from unit counts and a nominal clock.  Launches `blocks` x `threads` threads, each running 8 independent

@@ -51,7 +51,8 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_fields", "pt_trace_update", "pt_save", "pt_load", "pt_autotune", "pt_counters", "pt_sync", "pt_destroy",
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
            "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_set_global_sampler", "pt_gemm_bf16",
-           "pt_energy_fp64_static", "pt_fma_probe", "pt_fmc_graph", "pt_create_graph", "pt_check_wait"]
+           "pt_energy_fp64_static", "pt_fma_probe", "pt_fmc_graph", "pt_create_graph", "pt_check_wait",
+           "pt_graph_records"]
 
 _lib = None
 
@@ -103,6 +104,7 @@ def lib() -> ctypes.CDLL:
         L.pt_gemm_bf16.argtypes = [i, i, i, i, vp, vp, vp, vp]
         L.pt_energy_fp64_static.argtypes = [i, i, vp, vp, vp, d, vp]
         L.pt_fma_probe.argtypes = [i, i, i, i, vp, vp]
+        L.pt_graph_records.argtypes = [i, i64, vp, vp, vp, vp, vp]
         L.pt_last_error.argtypes = [vp]; L.pt_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -128,6 +130,19 @@ def fmc_graph(omega, gamma=None) -> np.ndarray:
 def fma_probe(packed, blocks, threads, iters, sink_ptr, stream_ptr):
     """Launches the FP32 FMA-pipe probe (pt_fma_probe): blocks * threads * iters * 32 flops on the stream."""
     _check(None, lib().pt_fma_probe(int(packed), int(blocks), int(threads), int(iters), sink_ptr, stream_ptr))
+
+
+def graph_records(N, quads, J):
+    """Incidence records of the FP32 quadruplet-list kernels (pt_graph_records): (offsets [N+1], rec [4 nq, 4]
+    int32 (A, B, C, w), recJ [4 nq] float32)."""
+    quads = np.ascontiguousarray(quads, np.int32).reshape(-1, 4)
+    J = np.ascontiguousarray(J, np.float64)
+    nq = len(quads)
+    off = np.zeros(int(N) + 1, np.int32)
+    rec = np.zeros((max(4 * nq, 1), 4), np.int32)
+    recJ = np.zeros(max(4 * nq, 1), np.float32)
+    _check(None, lib().pt_graph_records(int(N), nq, _p(quads), _p(J), _p(off), _p(rec), _p(recJ)))
+    return off, rec[: 4 * nq], recJ[: 4 * nq]
 
 
 def enumerate_quads(N: int) -> np.ndarray:

@@ -671,6 +671,51 @@ int set_shape(pt_ctx *c, int G, int ncw, int spu) {
     return PT_OK;
 }
 
+// Incidence lists of one quadruplet list (nq quadruplets of N modes, 4 ints each): inc[off[l] .. off[l+1]) are
+// the indices of the quadruplets holding mode l, in list order.  off: N+1 ints; inc: 4 nq ints.
+void incidence_lists(int N, int64_t nq, const int32_t *abcd, int *off, int *inc) {
+    std::fill(off, off + N + 1, 0);
+    for (int64_t q = 0; q < nq; ++q)
+        for (int m = 0; m < 4; ++m) off[abcd[4 * q + m] + 1]++;
+    for (int l = 0; l < N; ++l) off[l + 1] += off[l];
+    std::vector<int> fill(N, 0);
+    for (int64_t q = 0; q < nq; ++q)
+        for (int m = 0; m < 4; ++m) {
+            const int l = abcd[4 * q + m];
+            inc[off[l] + fill[l]++] = (int)q;
+        }
+}
+
+// Incidence records of the FP32 quadruplet-list kernels, one per (mode l, quadruplet q holding it) in the
+// order of the incidence lists: the other three modes A, B, C as row offsets of the kernel's amplitude table
+// (mode x kGraphRowStride), ordered so that l's field term is J a_A a_B conj(a_C) (the term of q is
+// J conj(a_q0) a_q1 a_q2 conj(a_q3); the field of a mode at position 1 or 2 is the conjugate of its product
+// of the other three factors), the positions of l, A, B, C packed in w (2 bits each), and J_q in FP32.
+void incidence_records(int N, const int32_t *abcd, const double *J, const int *off, const int *inc, int4 *rec,
+                       float *recJ) {
+    for (int l = 0; l < N; ++l)
+        for (int e = off[l]; e < off[l + 1]; ++e) {
+            const int q = inc[e];
+            const int32_t *m4 = abcd + 4 * (int64_t)q;
+            int pos = 0, o[3] = {0, 0, 0}, n = 0;
+            for (int m = 0; m < 4; ++m) {
+                if (m4[m] == l) pos = m;
+                else if (n < 3) o[n++] = m4[m];
+            }
+            // partner positions in ascending order (the positions other than pos), then the order A, B, C:
+            // pos 0 -> (1, 2, 3); pos 1 -> (0, 3, 2); pos 2 -> (0, 3, 1); pos 3 -> (1, 2, 0)
+            int op[3], n2 = 0;
+            for (int m = 0; m < 4; ++m)
+                if (m != pos) op[n2++] = m;
+            const int perm[4][3] = {{0, 1, 2}, {0, 2, 1}, {0, 2, 1}, {1, 2, 0}};
+            const int *pm = perm[pos];
+            const int R = ptgb::kGraphRowStride;
+            rec[e] = make_int4(o[pm[0]] * R, o[pm[1]] * R, o[pm[2]] * R,
+                               pos | (op[pm[0]] << 2) | (op[pm[1]] << 4) | (op[pm[2]] << 6));
+            recJ[e] = (float)J[q];
+        }
+}
+
 void free_all(pt_ctx *c) {
     drop_graphs(c);
     for (auto &p : c->allocs) {
@@ -779,6 +824,22 @@ int pt_create_graph(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t 
     if (!quads) return fail(nullptr, PT_EINVAL, "pt_create_graph: quads is NULL");
     return create_impl(out, cfg_in, S, Nv, quads, J, q_offsets, n_T, temps, replicas, seed, alloc, free_,
                        alloc_user, stream);
+}
+
+int pt_graph_records(int N, int64_t nq, const int32_t *quads, const double *J, int32_t *offsets, int32_t *rec,
+                     float *recJ) {
+    if (N < 4 || N > 2048 || nq < 0 || nq > (int64_t)1 << 28 || (nq > 0 && (!quads || !J)) || !offsets || (nq > 0 && (!rec || !recJ)))
+        return fail(nullptr, PT_EINVAL, "pt_graph_records: need 4 <= N <= 2048, 0 <= nq <= 2^28, quads, J, offsets, rec, recJ");
+    for (int64_t i = 0; i < 4 * nq; ++i)
+        if (quads[i] < 0 || quads[i] >= N) return fail(nullptr, PT_EINVAL, "pt_graph_records: mode index out of range");
+    std::vector<int> inc((size_t)std::max<int64_t>(4 * nq, 1));
+    incidence_lists(N, nq, quads, offsets, inc.data());
+    if (nq > 0) {
+        std::vector<int4> r((size_t)(4 * nq));  // int4 is 16-byte aligned; the caller's buffer need not be
+        incidence_records(N, quads, J, offsets, inc.data(), r.data(), recJ);
+        std::memcpy(rec, r.data(), r.size() * sizeof(int4));
+    }
+    return PT_OK;
 }
 
 static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const int32_t *graph,
@@ -987,6 +1048,8 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         std::vector<int4> hq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<double> hJq((size_t)std::max<int64_t>(q_off, 1));
         std::vector<int> hinc_off, hinc((size_t)std::max<int64_t>(inc_total, 1));
+        std::vector<int4> hrec(c->gfp32 ? hinc.size() : 0);
+        std::vector<float> hrecJ(c->gfp32 ? hinc.size() : 0);
         for (int s = 0; s < S; ++s) {
             const int n = c->N[s];
             const SampleDev &sd = c->samples[s];
@@ -994,21 +1057,17 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
             int64_t cnt = sd.nq;
             if (graph) std::copy(graph + 4 * J_offsets[s], graph + 4 * J_offsets[s + 1], abcd.begin());
             else pt_enumerate_quads(n, abcd.data(), &cnt);
-            std::vector<int> deg(n + 1, 0);
             for (int64_t q = 0; q < cnt; ++q) {
                 hq[sd.q_off + q] = make_int4(abcd[4 * q], abcd[4 * q + 1], abcd[4 * q + 2], abcd[4 * q + 3]);
                 hJq[sd.q_off + q] = J[J_offsets[s] + q];
-                for (int m = 0; m < 4; ++m) deg[abcd[4 * q + m] + 1]++;
             }
-            for (int l = 0; l < n; ++l) c->max_deg = std::max(c->max_deg, deg[l + 1]);
-            for (int l = 0; l < n; ++l) deg[l + 1] += deg[l];
-            std::vector<int> fill(n, 0);
-            for (int64_t q = 0; q < cnt; ++q)
-                for (int m = 0; m < 4; ++m) {
-                    const int l = abcd[4 * q + m];
-                    hinc[sd.inc_off + deg[l] + fill[l]++] = (int)q;
-                }
-            hinc_off.insert(hinc_off.end(), deg.begin(), deg.end());
+            std::vector<int> off(n + 1);
+            incidence_lists(n, cnt, abcd.data(), off.data(), hinc.data() + sd.inc_off);
+            for (int l = 0; l < n; ++l) c->max_deg = std::max(c->max_deg, off[l + 1] - off[l]);
+            hinc_off.insert(hinc_off.end(), off.begin(), off.end());
+            if (c->gfp32)
+                incidence_records(n, abcd.data(), J + J_offsets[s], off.data(), hinc.data() + sd.inc_off,
+                                  hrec.data() + sd.inc_off, hrecJ.data() + sd.inc_off);
         }
         RC(dalloc(c, &c->d_quads, hq.size()));
         RC(dalloc(c, &c->d_Jq, hJq.size()));
@@ -1019,39 +1078,6 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         CK(cudaMemcpy(c->d_inc_off, hinc_off.data(), hinc_off.size() * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->d_inc, hinc.data(), hinc.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (c->gfp32) {
-            // incidence records: for each mode l and quadruplet q holding it, the other three modes A, B, C
-            // as row offsets of the kernel's amplitude table, ordered so that l's field term is
-            // J a_A a_B conj(a_C) (positions 0 and 3 are conjugated in the term; the field of a mode at
-            // position 1 or 2 is the conjugate), and the four positions packed in w; J_q alongside
-            std::vector<int4> hrec(hinc.size());
-            std::vector<float> hrecJ(hinc.size());
-            for (int s = 0; s < S; ++s) {
-                const SampleDev &sd = c->samples[s];
-                const int *off = hinc_off.data() + sd.mode_off;
-                for (int l = 0; l < c->N[s]; ++l)
-                    for (int e = off[l]; e < off[l + 1]; ++e) {
-                        const int q = hinc[sd.inc_off + e];
-                        const int4 Q = hq[sd.q_off + q];
-                        const int m4[4] = {Q.x, Q.y, Q.z, Q.w};
-                        int pos = 0, o[3] = {0, 0, 0}, n = 0;
-                        for (int m = 0; m < 4; ++m) {
-                            if (m4[m] == l) pos = m;
-                            else if (n < 3) o[n++] = m4[m];
-                        }
-                        // partner positions in ascending order (the positions other than pos), then the
-                        // order A, B, C: pos 0 -> (1, 2, 3); pos 1 -> (0, 3, 2); pos 2 -> (0, 3, 1); pos 3 -> (1, 2, 0)
-                        int op[3], n2 = 0;
-                        for (int m = 0; m < 4; ++m)
-                            if (m != pos) op[n2++] = m;
-                        const int perm[4][3] = {{0, 1, 2}, {0, 2, 1}, {0, 2, 1}, {1, 2, 0}};
-                        const int *pm = perm[pos];
-                        const int R = ptgb::kGraphRowStride;
-                        hrec[sd.inc_off + e] =
-                            make_int4(o[pm[0]] * R, o[pm[1]] * R, o[pm[2]] * R,
-                                      pos | (op[pm[0]] << 2) | (op[pm[1]] << 4) | (op[pm[2]] << 6));
-                        hrecJ[sd.inc_off + e] = (float)hJq[sd.q_off + q];
-                    }
-            }
             RC(dalloc(c, &c->d_rec, hrec.size()));
             RC(dalloc(c, &c->d_recJ, hrecJ.size()));
             CK(cudaMemcpy(c->d_rec, hrec.data(), hrec.size() * sizeof(int4), cudaMemcpyHostToDevice));

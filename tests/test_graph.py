@@ -108,3 +108,53 @@ def test_sparse_comb_graph(N, z):
     if N == 64:  # every listed quadruplet belongs to the comb list
         comb = {tuple(q) for q in oracle.enumerate_quads(N).tolist()}
         assert all(tuple(q) in comb for q in g.tolist())
+
+
+@pytest.mark.parametrize("kind", ["random", "comb", "sparse"])
+def test_incidence_records_decode_to_the_oracle_fields(kind):
+    """The FP32 quadruplet-list kernels read one record per (mode, quadruplet holding it): three row offsets
+    A, B, C and the positions of the four factors, so that the term is J a_A a_B conj(a_C).  Decoded on the
+    host, every record must give the oracle's contribution of its quadruplet to the local field of its mode
+    (Sec. III.A.3), the positions must name where each mode sits, and the records of a mode must sum to the
+    oracle's whole field: a wrong permutation entry for one position would fail here."""
+    rng = np.random.default_rng(7)
+    if kind == "random":
+        N = 14
+        quads = pkg.fmc_graph(workload.random_frequencies(N, 91))
+    elif kind == "comb":
+        N = 12
+        quads = oracle.enumerate_quads(N)
+    else:
+        N = 64
+        quads = workload.sparse_comb_graph(N, 6, 5)
+    J = rng.standard_normal(len(quads)) / N
+    off, rec, recJ = pkg.graph_records(N, quads, J)
+    a = np.sqrt(rng.uniform(0.3, 1.5, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, N))
+    J32 = J.astype(np.float32).astype(np.float64)
+    splittings = set()
+    for l in range(N):
+        held = [q for q in range(len(quads)) if l in quads[q]]
+        assert off[l + 1] - off[l] == len(held)
+        tot = 0j
+        for e, q in zip(range(off[l], off[l + 1]), held):
+            A, B, C, w = (int(v) for v in rec[e])
+            assert A % 9 == 0 and B % 9 == 0 and C % 9 == 0
+            mA, mB, mC = A // 9, B // 9, C // 9
+            pos, pA, pB, pC = w & 3, (w >> 2) & 3, (w >> 4) & 3, (w >> 6) & 3
+            assert sorted([pos, pA, pB, pC]) == [0, 1, 2, 3]
+            assert quads[q][pos] == l and quads[q][pA] == mA and quads[q][pB] == mB and quads[q][pC] == mC
+            assert recJ[e] == np.float32(J[q])
+            term = float(recJ[e]) * a[mA] * a[mB] * np.conj(a[mC])
+            ref = oracle.field(N, quads[q:q + 1], J32[q:q + 1], a, l)
+            assert abs(term - ref) <= 1e-12 * (abs(ref) + 1e-300), (l, q, pos, term, ref)
+            splittings.add(pos)
+            tot += term
+        assert abs(tot - oracle.field(N, quads, J32, a, l)) <= 1e-11 * (abs(tot) + 1e-3)
+    assert splittings == {0, 1, 2, 3}
+
+
+def test_incidence_records_reject_bad_lists():
+    with pytest.raises(pkg.PTError):
+        pkg.graph_records(8, np.array([[0, 1, 2, 9]]), np.ones(1))
+    with pytest.raises(pkg.PTError):
+        pkg.graph_records(3, np.array([[0, 1, 2, 3]]), np.ones(1))
