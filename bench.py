@@ -59,6 +59,23 @@ def flops_per_chain_sweep(N: int) -> float:
     return tot / (N * (N - 1)) * (N / 2)
 
 
+def count_quads(N: int) -> int:
+    """|Q| of the N-mode comb: pairs {x<y} grouped by their sum s; every two pairs of one sum make one
+    quadruplet."""
+    m = np.zeros(2 * N, np.int64)
+    for x in range(N):
+        for y in range(x + 1, N):
+            m[x + y] += 1
+    return int((m * (m - 1) // 2).sum())
+
+
+def survey_flops_per_chain_sweep(N: int) -> float:
+    """Algorithmic work of one chain-sweep as the hot-path scope counts it: 4|Q| coupling terms (every term
+    is visited by each of its 4 modes once per sweep on average: N/2 pair updates x 2 fields x 4|Q|/N
+    terms), 16 FP32 flops each (two complex multiplies, a real scale, an add)."""
+    return 16.0 * 4.0 * count_quads(N)
+
+
 def profiled_traffic():
     """DRAM bytes per bench sweep launch from the committed ncu summary, or None if the kernel source changed
     since the counters were taken."""
@@ -78,8 +95,44 @@ def profiled_traffic():
 
 
 def peak_fp32_tflops(sm_count=152, mhz=2070.0):
-    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    """FP32 FMA peak from unit counts: SMs x 128 FP32 lanes x 2 flops x clock (context for the measured one)."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measure_fp32_peak(reps=3, target_ms=60.0):
+    """Measured FP32 fused multiply-add throughput (pt_fma_probe): 8 resident blocks of 256 threads per SM
+    (SM count read from the device), each thread 8 independent chains; packed (paired FMA) and scalar
+    variants, one warm-up launch each, then `reps` launches timed with CUDA events on one stream; the
+    larger rate is the peak.  Returns TFLOP/s and the details."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = int(props.multi_processor_count)
+    blocks, threads = sms * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"sm_count": sms, "blocks": blocks, "threads": threads}
+    for packed in (1, 0):
+        iters = 2000
+        for _ in range(3):  # calibrate the launch to about target_ms
+            pkg.fma_probe(packed, blocks, threads, iters, sink.data_ptr(), stream.cuda_stream)
+            ev0.record(stream)
+            pkg.fma_probe(packed, blocks, threads, iters, sink.data_ptr(), stream.cuda_stream)
+            ev1.record(stream)
+            stream.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            iters = max(100, int(iters * target_ms / max(ms, 1e-3)))
+        ev0.record(stream)
+        for _ in range(reps):
+            pkg.fma_probe(packed, blocks, threads, iters, sink.data_ptr(), stream.cuda_stream)
+        ev1.record(stream)
+        stream.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        out["packed" if packed else "scalar"] = blocks * threads * iters * 32.0 * reps / sec / 1e12
+        out["iters"] = iters
+    out["tflops"] = max(out["packed"], out["scalar"])
+    return out
 
 
 # ------------------------------------------------------------------------------------------- clocks
@@ -179,6 +232,58 @@ def whole_job_rate(units_per_rank, world, ms):
     return units_per_rank * world / (ms / 1e3)
 
 
+def _free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def _rank_entry(rank, world, port, target, args, init_group, backend):
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world), LOCAL_WORLD_SIZE=str(world),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist = None
+    if init_group:
+        import torch.distributed as dist
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    try:
+        rc = target(rank, world, dist, *args)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+    sys.exit(int(rc or 0))
+
+
+def spawn_ranks(world, target, args=(), init_group=True, backend="gloo", timeout=3600.0):
+    """One process per rank on this node (spawned, so no CUDA state is inherited), each with RANK, LOCAL_RANK,
+    WORLD_SIZE and MASTER_ADDR/PORT (127.0.0.1) set as a launcher would, running target(rank, world, dist,
+    *args) (dist: the joined process group when init_group, else None and the target joins it).  Returns the
+    exit codes in rank order."""
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_entry, args=(r, world, port, target, tuple(args), init_group, backend))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    t0 = time.time()
+    for p in procs:
+        p.join(timeout=max(1.0, timeout - (time.time() - t0)))
+    codes = []
+    for p in procs:
+        if p.is_alive():
+            p.terminate()
+            p.join(timeout=10)
+            codes.append(-1)
+        else:
+            codes.append(p.exitcode)
+    return codes
+
+
+def _bench_rank(rank, world, dist, argv):
+    """A rank started by `bench.py --gpus N` itself: the same path as under torchrun."""
+    return main(argv)
+
+
 # ------------------------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, dist):
     import torch
@@ -230,11 +335,14 @@ def run_gpu(args, rank, world, dist):
     ev1.record(stream)
     torch.cuda.synchronize()
     kms = ev0.elapsed_time(ev1) / reps
-    fl = flops_per_chain_sweep(N_MODES) * chains * STEP_SWEEPS
+    fl_exec = flops_per_chain_sweep(N_MODES) * chains * STEP_SWEEPS
+    fl = survey_flops_per_chain_sweep(N_MODES) * chains * STEP_SWEEPS
     clocks = clk.summary()
-    peak = peak_fp32_tflops()
-    achieved = fl / (kms / 1e3) / 1e12
     pk.close()
+    probe = measure_fp32_peak()
+    peak = probe["tflops"]
+    achieved = fl / (kms / 1e3) / 1e12
+    achieved_exec = fl_exec / (kms / 1e3) / 1e12
 
     # ---- plain FP64 GPU sweep (paper's design) on the same workload, bounded sample
     pp = pkg.PT(W.Ns, Js, W.temps, W.replicas, 4242, precision="fp64_plain", stream=stream, **kw)
@@ -265,8 +373,8 @@ def run_gpu(args, rank, world, dist):
     e2e = {"value": chains * STEP_SWEEPS * e2e_steps * world / wall, "unit": "chain-sweeps/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     pt.close()
-    return dict(value=value, ms=ms, kms=kms, achieved=achieved, peak=peak, clocks=clocks, plain_rate=plain_rate,
-                e2e=e2e, fl=fl)
+    return dict(value=value, ms=ms, kms=kms, achieved=achieved, achieved_exec=achieved_exec, peak=peak, probe=probe,
+                clocks=clocks, plain_rate=plain_rate, e2e=e2e, fl=fl, fl_exec=fl_exec)
 
 
 def learned_leg():
@@ -340,7 +448,7 @@ def graph_leg(sweeps=64, plain_sweeps=4):
                                              "x 2 replicas, FP32 group kernels"}}
 
 
-def workloads_leg(sweeps=64):
+def workloads_leg(sweeps=64, peak32=None):
     """The other synthetic workloads at 1 GPU, each a PT run with its own swap (64), measurement (16) and
     resync (64) schedule: chain-sweeps/s from CUDA events on the library's stream over `sweeps` sweeps after
     2 warm-up sweeps, and the achieved fraction of the derived peak (FP32, or FP64 for the FP64 path) from
@@ -370,20 +478,60 @@ def workloads_leg(sweeps=64):
         torch.cuda.synchronize()
         sec = ev0.elapsed_time(ev1) / 1e3
         per_chain = W.replicas * len(W.temps)
-        fl = 0.0
+        fl = fl_x = 0.0
         for n in W.Ns:
             if n not in fl_cache:
-                fl_cache[n] = flops_per_chain_sweep(n)
-            fl += fl_cache[n] * per_chain * sweeps
-        peak = peak_fp32_tflops() if prec == "fp32" else peak64
+                fl_cache[n] = (survey_flops_per_chain_sweep(n), flops_per_chain_sweep(n))
+            fl += fl_cache[n][0] * per_chain * sweeps
+            fl_x += fl_cache[n][1] * per_chain * sweeps
+        if prec == "fp32":
+            peak = peak32 if peak32 else peak_fp32_tflops()
+            basis = "measured FP32 FMA peak (pt_fma_probe)" if peak32 else "FP32 unit-count peak at 2070 MHz"
+        else:
+            peak, basis = peak64, "2 FP64 FMA/SM/clock x 152 SMs x 2070 MHz"
         achieved = fl / sec / 1e12
         out[key] = {"value": pt.n_chains * sweeps / sec, "unit": "chain-sweeps/s", "precision": prec,
                     "chains": pt.n_chains, "N": sorted(set(int(n) for n in W.Ns)), "sweeps": sweeps,
                     "achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak,
-                    "peak_basis": "derived FP32 peak" if prec == "fp32" else "2 FP64 FMA/SM/clock x 152 SMs x 2070 MHz",
-                    "autotuned_shape": list(shape) if shape else None}
+                    "frac_executed": fl_x / sec / 1e12 / peak,
+                    "flop_count": "16 flops x 4|Q| per chain-sweep (frac); pair-factored executed count (frac_executed)",
+                    "peak_basis": basis, "autotuned_shape": list(shape) if shape else None}
         pt.close()
     return out
+
+
+def precision_leg(burn=512, sweeps=4096):
+    """FP32 against FP64 on the batched N=64 workload (64 samples x 32 T [0.3,1.6] x 2 replicas; each path's
+    default block shape): the same couplings and seeds (common random numbers), `burn` sweeps, then `sweeps`
+    sweeps measured every 16.  Per observable the disorder-averaged FP32 - FP64 difference per temperature
+    with its paired jackknife error over samples (analysis.paired_difference), summarised over temperatures.
+    The FP64 J-sharing path follows the oracle's chain to 1e-9, so it stands for the oracle here."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import analysis, workload
+    W = workload.workloads()["n64_batched"]
+    nq = len(pkg.enumerate_quads(64))
+    Js = [workload.couplings(64, nq, sd) for sd in W.seeds]
+    obs, secs = {}, {}
+    for prec in ("fp32", "fp64"):
+        pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 61, precision=prec, stream=torch.cuda.Stream(),
+                    swap_every=64, measure_every=16, resync_every=64)
+        t0 = time.perf_counter()
+        pt.sweep(burn)
+        pt.reset_observables()
+        pt.sweep(sweeps)
+        obs[prec] = pt.observables()
+        secs[prec] = time.perf_counter() - t0
+        pt.close()
+    d = analysis.paired_difference(obs["fp32"], obs["fp64"], W.temps, 64)
+    summ = analysis.difference_summary(d)
+    tmin = {k: {"diff": float(v["diff"][0]), "err": float(v["err"][0]), "ref": float(v["ref"][0])}
+            for k, v in d.items() if k != "Pq"}
+    return {"workload": "n64_batched: N=64 comb, 64 samples x 32 T [0.3,1.6] x 2 replicas",
+            "burn": burn, "sweeps": sweeps, "measure_every": 16,
+            "reference": "FP64 J-sharing GPU path, same seeds (follows the FP64 oracle's chain to 1e-9)",
+            "observables": "E/N, C_V/N, <q^2>, <q^4>, Y2, Y4 per (sample, T); P_J(q) on 20 coarse bins",
+            "summary": summ, "at_T_min": tmin, "wall_s": secs}
 
 
 def ladder_leg():
@@ -438,6 +586,42 @@ def profile_case():
     return 0
 
 
+def profile_small():
+    """Small cases for ncu, a few launches each: the batched N=64 workload itself (64 samples x 32 T x 2
+    replicas on the FP32 default 32 x 7 blocks: three 1-sweep launches; 26 MB of couplings, held by the L2 as
+    in the timed runs), then on N=256 (8 samples x 48 T x 2 replicas, 199 MB of couplings) one swap interval
+    of 16 sweeps with its resync (energy_kernel), measurement (measure_kernel) and swap pass (swap_kernel),
+    and the plain FP64 sweep (plain_sweep_kernel, the paper's design) for one sweep on 2 samples of N=64."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    pkg.build()
+    Wb = workload.workloads()["n64_batched"]
+    nq64 = len(pkg.enumerate_quads(64))
+    Js = [workload.couplings(64, nq64, s) for s in Wb.seeds]
+    pt = pkg.PT(Wb.Ns, Js, Wb.temps, 2, 5, precision="fp32", chains_per_block=32, consumer_warps=7,
+                swap_every=0, measure_every=0, resync_every=0, use_graphs=False)
+    for _ in range(3):
+        pt.sweep(1)
+    pt.sync()
+    pt.close()
+    W = workload.workloads()["n256_large"]
+    nq = len(pkg.enumerate_quads(N_MODES))
+    Js = [workload.couplings(N_MODES, nq, s) for s in W.seeds[:8]]
+    pt = pkg.PT(W.Ns[:8], Js, W.temps, W.replicas, 5, precision="fp32", swap_every=16, measure_every=16,
+                resync_every=16, use_graphs=False)
+    pt.sweep(16)
+    pt.sync()
+    pt.close()
+    pp = pkg.PT([64] * 2, [workload.couplings(64, nq64, s) for s in (1, 2)], Wb.temps, 2, 5,
+                precision="fp64_plain", swap_every=0, measure_every=0, resync_every=0, use_graphs=False)
+    pp.sweep(1)
+    pp.sync()
+    pp.close()
+    print("profile small done")
+    return 0
+
+
 def profile_global():
     """Eight learned global-move rounds on the learned-proposal workload (N=64, 16 samples x 32 T x 2 replicas,
     8 coldest temperatures, a round every 8 sweeps; untrained network): 64 sweeps.  For the launch list of a
@@ -488,7 +672,7 @@ def profile_graph():
     return 0
 
 
-def main():
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
@@ -499,19 +683,36 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the random-frequency graph leg")
     ap.add_argument("--no-ladder", action="store_true", help="skip the adaptive-ladder leg")
     ap.add_argument("--no-workloads", action="store_true", help="skip the leg of the other synthetic workloads")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 observable comparison")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="small cases for ncu: N=64 on 32 x 7 blocks, the N=256 resync/measure/swap kernels, the "
+                         "plain FP64 sweep")
     ap.add_argument("--profile-global", action="store_true",
                     help="run eight learned global-move rounds (for the launch list of a round) and exit")
     ap.add_argument("--profile-graph", action="store_true",
                     help="a few launches of the graph kernels (N=64 random graph, N=2048 sparse graph) and exit")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.profile_case:
         return profile_case()
+    if args.profile_small:
+        return profile_small()
     if args.profile_global:
         return profile_global()
     if args.profile_graph:
         return profile_graph()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start one rank per GPU here (weak scaling, samples sharded by rank_seeds)
+        if args.impl == "gb300":
+            import torch
+            if torch.cuda.device_count() < args.gpus:
+                print("bench.py: --gpus %d but %d CUDA devices visible" % (args.gpus, torch.cuda.device_count()),
+                      file=sys.stderr)
+                return 2
+        codes = spawn_ranks(args.gpus, _bench_rank, (list(sys.argv[1:] if argv is None else argv),),
+                            init_group=False)
+        return 0 if all(c == 0 for c in codes) else 1
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "n256_large: N=256 comb, 16 samples x 48 T [0.25,1.6] x 2 replicas, FP32 fields",
@@ -544,7 +745,9 @@ def main():
 
     dist = None
     if world > 1:
+        import torch
         import torch.distributed as dist_mod
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)) % torch.cuda.device_count())
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     r = run_gpu(args, rank, world, dist)
@@ -559,7 +762,10 @@ def main():
         ladder = ladder_leg()
     wl = None
     if rank == 0 and world == 1 and not args.no_workloads:
-        wl = workloads_leg()
+        wl = workloads_leg(peak32=r["peak"])
+    prec = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        prec = precision_leg()
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -567,9 +773,19 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
                              "frac": r["achieved"] / r["peak"], "traffic": profiled_traffic(),
-                             "kernel": "sweep_kernel<float,8,11> (8 chains x 11 field warps + 1 copy warp per block)", "kernel_ms_per_launch": r["kms"],
-                             "flops_per_launch": r["fl"],
-                             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)"},
+                             "kernel": "sweep_kernel<float,8,11> (8 chains x 11 field warps + 1 copy warp per block)",
+                             "kernel_ms_per_launch": r["kms"],
+                             "flop_count": "algorithmic: 16 FP32 flops x 4|Q| coupling terms per chain-sweep "
+                                           "(87.9 MFLOP at N=256)",
+                             "flops_per_launch": r["fl"], "frac_survey": r["achieved"] / r["peak"],
+                             "achieved_executed": r["achieved_exec"], "frac_executed": r["achieved_exec"] / r["peak"],
+                             "flops_per_launch_executed": r["fl_exec"],
+                             "executed_count": "flops the pair-factored kernel performs: 6 per pair product, 4 per "
+                                               "coupling term, 8 per field row (43.3 MFLOP per chain-sweep at N=256)",
+                             "peak_basis": "measured: pt_fma_probe, %d blocks x %d threads, packed %.1f / scalar %.1f "
+                                           "TFLOP/s (unit-count peak at the nominal 2070 MHz: %.1f)"
+                                           % (r["probe"]["blocks"], r["probe"]["threads"], r["probe"]["packed"],
+                                              r["probe"]["scalar"], peak_fp32_tflops(r["probe"]["sm_count"]))},
                 "cpu_baseline": cpu,
                 "e2e": r["e2e"],
                 "clocks": r["clocks"],
@@ -579,7 +795,8 @@ def main():
                 "learned_vs_plain": learned,
                 "random_graph": graph,
                 "adaptive_ladder": ladder,
-                "workloads": wl}
+                "workloads": wl,
+                "precision_error": prec}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -151,3 +151,62 @@ def adaptive_ladder(T_grid, CV_grid, T_min: float, T_max: float, C: float = 0.6,
     if out[-1] < T_max:
         out.append(float(T_max))
     return np.asarray(out)
+
+
+def overlap_distribution(qhist: np.ndarray, width: int = 10) -> np.ndarray:
+    """P_J(q) per (sample, T), normalised per sample (Sec. IV.C), on coarse bins of `width` fine bins (the
+    201 fine bins centred at -1, -0.99, ..., 1; the last coarse bin also takes the fine bin at q = 1)."""
+    h = np.asarray(qhist, np.float64)
+    nb = (h.shape[-1] - 1) // width
+    coarse = h[..., : nb * width].reshape(h.shape[:-1] + (nb, width)).sum(-1)
+    coarse[..., -1] += h[..., nb * width:].sum(-1)
+    tot = coarse.sum(-1, keepdims=True)
+    return coarse / np.where(tot > 0, tot, 1.0)
+
+
+def paired_difference(obs_a: dict, obs_b: dict, temps, N, pq_min_mass: float = 1e-3) -> dict:
+    """Disorder-averaged difference a - b of the observables of two runs on the same disorder samples
+    (paired over samples, e.g. FP32 against FP64): per temperature the jackknife mean and error of the
+    per-sample differences of E/N, C_V/N (Eq. (21)), <q^2>, <q^4> (Sec. IV.C), Y2, Y4 (Sec. IV.D), the scale
+    of each observable (the disorder average of run b) and z = difference / error; for P_J(q) on coarse bins
+    the same per (T, bin) where run b's mass is at least pq_min_mass."""
+    ta, tb = thermal_averages(obs_a, temps), thermal_averages(obs_b, temps)
+    scale = {"E": 1.0 / N, "CV": 1.0 / N, "q2": 1.0, "q4": 1.0, "Y2": 1.0, "Y4": 1.0}
+    out = {}
+    for key, f in scale.items():
+        d, err = jackknife(f * (ta[key] - tb[key]))
+        ref, _ = jackknife(f * tb[key])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            z = np.where(err > 0, d / err, 0.0)
+        out[key] = {"diff": d, "err": err, "ref": ref, "z": z}
+    pa, pb = overlap_distribution(obs_a["qhist"]), overlap_distribution(obs_b["qhist"])
+    d, err = jackknife(pa - pb)
+    ref = pb.mean(0)
+    use = (ref >= pq_min_mass) & (err > 0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        z = np.where(use, d / np.where(err > 0, err, 1.0), 0.0)
+    out["Pq"] = {"diff": d, "err": err, "ref": ref, "z": z, "used": use}
+    return out
+
+
+def difference_summary(diff: dict) -> dict:
+    """Per observable of paired_difference: the largest |difference| over temperatures (and its error), the
+    mean over temperatures of |difference| / |disorder average| (P(q): of |difference| summed over bins), the
+    mean of z^2 (about 1 when the two runs sample the same law) and the largest |z|."""
+    out = {}
+    for key, v in diff.items():
+        d, e, z = np.asarray(v["diff"]), np.asarray(v["err"]), np.asarray(v["z"])
+        if key == "Pq":
+            u = v["used"]
+            out[key] = {"max_abs_diff": float(np.abs(d[u]).max()) if u.any() else 0.0,
+                        "l1_diff_mean_over_T": float(np.abs(d).sum(-1).mean()),
+                        "mean_z2": float((z[u] ** 2).mean()) if u.any() else 0.0,
+                        "max_abs_z": float(np.abs(z[u]).max()) if u.any() else 0.0, "bins_used": int(u.sum())}
+            continue
+        i = int(np.argmax(np.abs(d)))
+        ref = np.abs(np.asarray(v["ref"]))
+        rel = np.abs(d) / np.where(ref > 0, ref, np.inf)
+        out[key] = {"max_abs_diff": float(abs(d[i])), "err_at_max": float(e[i]),
+                    "mean_rel_diff": float(rel.mean()), "mean_z2": float((z ** 2).mean()),
+                    "max_abs_z": float(np.abs(z).max())}
+    return out

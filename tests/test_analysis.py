@@ -126,3 +126,64 @@ def test_adaptive_ladder_solves_the_implicit_recursion():
 def test_adaptive_ladder_rejects_too_small_specific_heat():
     with pytest.raises(ValueError):
         analysis.adaptive_ladder([0.1, 2.0], [0.25, 0.25], 0.2, 1.0, 0.6)
+
+
+def _synthetic_obs(rng, S, T, E_shift=0.0, q_sd=0.3, n=400):
+    """Accumulators of S samples x T temperatures built from explicit per-sample draws."""
+    stat = np.zeros((S, T, 7)); qstat = np.zeros((S, T, 5)); qhist = np.zeros((S, T, 201), np.uint64)
+    for s in range(S):
+        for t in range(T):
+            E = rng.normal(-1.0 + 0.1 * s + E_shift, 0.5, n)
+            Y = rng.uniform(0.01, 0.02, n)
+            stat[s, t] = [n, E.sum(), (E * E).sum(), Y.sum(), (Y * Y).sum(), n * 8.0, n * 64.0]
+            q = np.clip(rng.normal(0.0, q_sd, n), -1, 1)
+            qstat[s, t] = _qstat_from_samples(q)
+            np.add.at(qhist[s, t], np.floor(100 * (q + 1) + 0.5).astype(int), 1)
+    return {"stat": stat, "qstat": qstat, "qhist": qhist}
+
+
+def test_overlap_distribution_coarse_bins():
+    h = np.zeros((1, 1, 201), np.uint64)
+    h[0, 0, 0] = 3; h[0, 0, 9] = 1; h[0, 0, 10] = 4; h[0, 0, 200] = 2
+    P = analysis.overlap_distribution(h)
+    assert P.shape == (1, 1, 20)
+    assert np.allclose(P[0, 0, :2], [0.4, 0.4]) and P[0, 0, -1] == pytest.approx(0.2) and P.sum() == pytest.approx(1.0)
+
+
+def test_paired_difference_recovers_a_known_shift_and_zero():
+    rng = np.random.default_rng(11)
+    S, T, N = 12, 3, 16
+    a = _synthetic_obs(np.random.default_rng(5), S, T)
+    b = {k: v.copy() for k, v in a.items()}
+    same = analysis.paired_difference(a, b, [0.5, 1.0, 1.5], N)
+    for key in ("E", "CV", "q2", "q4", "Y2", "Y4"):
+        assert np.all(same[key]["diff"] == 0.0), key
+    assert np.all(same["Pq"]["diff"] == 0.0)
+    # shift every energy of run a by delta: <E>/N moves by delta/N, C_V (a variance) does not move
+    delta = 0.37
+    a2 = {k: v.copy() for k, v in a.items()}
+    n = a2["stat"][..., 0]
+    a2["stat"][..., 2] += 2 * delta * a2["stat"][..., 1] + n * delta ** 2
+    a2["stat"][..., 1] += n * delta
+    d = analysis.paired_difference(a2, b, [0.5, 1.0, 1.5], N)
+    assert np.allclose(d["E"]["diff"], delta / N, rtol=1e-12)
+    assert np.allclose(d["CV"]["diff"], 0.0, atol=1e-12)
+    assert np.allclose(d["E"]["err"], 0.0, atol=1e-12)
+    summ = analysis.difference_summary(d)
+    assert summ["E"]["max_abs_diff"] == pytest.approx(delta / N)
+    del rng
+
+
+def test_paired_difference_z_of_independent_runs_is_standard():
+    """Two independent runs of the same law: the z of the paired differences are about standard normal
+    (mean z^2 near 1), and a real shift of 0.05 in <q^2> gives large z."""
+    S, T = 16, 40
+    a = _synthetic_obs(np.random.default_rng(21), S, T)
+    b = _synthetic_obs(np.random.default_rng(22), S, T)
+    d = analysis.paired_difference(a, b, np.linspace(0.5, 1.5, T), 16)
+    for key in ("E", "CV", "q2", "Y4"):
+        assert 0.5 < float((d[key]["z"] ** 2).mean()) < 1.8, key
+    assert 0.5 < analysis.difference_summary(d)["Pq"]["mean_z2"] < 1.8
+    c = _synthetic_obs(np.random.default_rng(23), S, T, q_sd=0.38)
+    d2 = analysis.paired_difference(c, b, np.linspace(0.5, 1.5, T), 16)
+    assert np.abs(d2["q2"]["z"]).min() > 5
