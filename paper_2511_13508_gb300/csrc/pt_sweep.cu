@@ -508,7 +508,7 @@ template <typename real, int G, int NCW> struct SweepShape {
     static constexpr size_t stage_bytes = (size_t)2 * CB * JS * sizeof(real);
     // ring depth: as many stages (3..6) as fit next to an N = 256 amplitude table in ~210 KB, so that the
     // copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs)
-    static constexpr bool PACKED = sizeof(real) == 4 && G == 8;  // packed-FP32 block arithmetic
+    static constexpr bool PACKED = sizeof(real) == 4;  // packed-FP32 block arithmetic (every FP32 shape)
     static constexpr size_t amp_bytes_256 = (size_t)(256 + 2 * APAD) * RS * 2 * sizeof(real) +
                                             (PACKED ? (size_t)(256 + 2 * APAD) * G * sizeof(float4) : 0);
     static constexpr int NST_FIT = (int)((210 * 1024 - amp_bytes_256 - 8 * 1024) / stage_bytes);

@@ -33,6 +33,15 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-5, "fp64": 1e-12}
 _QUADS = {}
+WORST = {}  # largest relative errors seen per precision (printed at the end of the module, with -s)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _report():
+    yield
+    for prec, w in WORST.items():
+        print("\ntrace %s: largest |GPU - oracle| / magnitude: fields %.2e, B/A %.2e, Delta H %.2e"
+              % (prec, w["h"], w["BA"], w["dH"]))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -79,6 +88,7 @@ def check_records(rec, a, Ns, Js, temps, R, nT, seed, sweep, update, chains, pre
     tol = TOL[prec]
     off = state_offsets(Ns, R, nT)
     checked = ambiguous = 0
+    worst = WORST.setdefault(prec, {"h": 0.0, "BA": 0.0, "dH": 0.0})
     for ci in chains:
         s, t = ci // (R * nT), ci % nT
         N = Ns[s]
@@ -97,6 +107,8 @@ def check_records(rec, a, Ns, Js, temps, R, nT, seed, sweep, update, chains, pre
         B_o, A_o = oracle.cross_terms(N, q, J, x, j, k)
         sj, sk = term_scale(q, J, x, [j]), term_scale(q, J, x, [k])
         sjk = term_scale(q, J, x, [j, k])
+        worst["h"] = max(worst["h"], abs(hj - hj_o) / max(abs(hj_o), sj), abs(hk - hk_o) / max(abs(hk_o), sk))
+        worst["BA"] = max(worst["BA"], abs(B - B_o) / max(abs(B_o), sjk, 1e-300), abs(A - A_o) / max(abs(A_o), sjk, 1e-300))
         assert abs(hj - hj_o) <= tol * max(abs(hj_o), sj), (ci, j, k, hj, hj_o)
         assert abs(hk - hk_o) <= tol * max(abs(hk_o), sk), (ci, j, k, hk, hk_o)
         assert abs(B - B_o) <= tol * max(abs(B_o), sjk) + 1e-300, (ci, j, k, B, B_o)
@@ -116,6 +128,7 @@ def check_records(rec, a, Ns, Js, temps, R, nT, seed, sweep, update, chains, pre
         dH, acc, beta = r_[15], r_[16], r_[17]
         dH_o = oracle.delta_h(N, q, J, x, j, k, nj, nk)
         dscale = abs(nj - x[j]) * sj + abs(nk - x[k]) * sk + abs(nj - x[j]) * abs(nk - x[k]) * sjk
+        worst["dH"] = max(worst["dH"], abs(dH - dH_o) / max(abs(dH_o), dscale))
         assert abs(dH - dH_o) <= tol * max(abs(dH_o), dscale), (ci, dH, dH_o, dscale)
         assert beta == pytest.approx(1.0 / temps[t], rel=1e-7 if prec == "fp32" else 1e-15)
         acc_o = dH_o <= 0.0 or U_o < np.exp(-beta * dH_o)
