@@ -500,6 +500,77 @@ def workloads_leg(sweeps=64, peak32=None):
     return out
 
 
+def _oracle_calibrate(N, nq):
+    """Seconds per chain-sweep of the oracle at N (one chain, enough sweeps for about 0.2 s)."""
+    sw = 1
+    while True:
+        _, t = _oracle_worker((N, nq, 301, sw, [0.5]))
+        if t > 0.2 or sw > 1 << 16:
+            return t / sw
+        sw *= 4
+
+
+def oracle_rate_mixed(Ns, target_seconds=3.0, workers=None):
+    """Oracle chain-sweeps/s on the host cores for a workload of mode counts Ns: one spawned process per core,
+    process i simulating two chains (T = 0.5 and 1.5) of one sample with N = Ns[i mod len(Ns)] for about
+    target_seconds."""
+    import oracle
+    workers = workers or os.cpu_count() or 1
+    Ns = [int(n) for n in Ns]
+    nqs = {n: len(oracle.enumerate_quads(n)) for n in set(Ns)}
+    cost = {n: _oracle_calibrate(n, nqs[n]) for n in set(Ns)}
+    jobs = []
+    for i in range(workers):
+        n = Ns[i % len(Ns)]
+        jobs.append((n, nqs[n], 501 + i, max(1, int(target_seconds / cost[n] / 2)), [0.5, 1.5]))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    return sum(r[0] for r in res) / wall, workers
+
+
+def baseline_table_leg(main_line):
+    """Every synthetic workload on every implementation, for the baseline table: the FP32 J-sharing path
+    (64 sweeps with the workload's schedule), the FP64 J-sharing path and the plain FP64 path (the paper's
+    design; bounded samples of sweeps), all timed with CUDA events on the library's stream, and the FP64 oracle
+    on the host cores (bounded sample).  chain-sweeps/s each."""
+    import torch
+    import paper_2511_13508_gb300 as pkg
+    from paper_2511_13508_gb300 import workload
+    Wall = workload.workloads()
+    out = {}
+    plan = {"n16_fp64": (64, 64, 16), "n64_batched": (64, 8, 2), "ragged": (64, 8, 2), "n256_large": (0, 1, 0),
+            "n64_learned": (64, 8, 2)}
+    for name, (s32, s64, splain) in plan.items():
+        W = Wall[name]
+        Js = [workload.couplings(n, len(pkg.enumerate_quads(n)), sd) for n, sd in zip(W.Ns, W.seeds)]
+        row = {"N": sorted(set(int(n) for n in W.Ns)), "chains": W.chains}
+        for prec, sw in (("fp32", s32), ("fp64", s64), ("fp64_plain", splain)):
+            if sw == 0:
+                continue
+            stream = torch.cuda.Stream()
+            pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 71, precision=prec, stream=stream, swap_every=64,
+                        measure_every=16, resync_every=64)
+            pt.sweep(1)
+            pt.sync()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            pt.sweep(sw)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            row[prec] = pt.n_chains * sw / (ev0.elapsed_time(ev1) / 1e3)
+            row[prec + "_sweeps"] = sw
+            pt.close()
+        if name == "n256_large":
+            row["fp32"] = main_line["value"]
+            row["fp64_plain"] = main_line["plain_rate"]
+        row["oracle"], row["oracle_cores"] = oracle_rate_mixed(W.Ns)
+        out[name] = row
+    return out
+
+
 def precision_leg(burn=512, sweeps=4096):
     """FP32 against FP64 on the batched N=64 workload (64 samples x 32 T [0.3,1.6] x 2 replicas; each path's
     default block shape): the same couplings and seeds (common random numbers), `burn` sweeps, then `sweeps`
@@ -684,6 +755,7 @@ def main(argv=None):
     ap.add_argument("--no-ladder", action="store_true", help="skip the adaptive-ladder leg")
     ap.add_argument("--no-workloads", action="store_true", help="skip the leg of the other synthetic workloads")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 observable comparison")
+    ap.add_argument("--no-table", action="store_true", help="skip the every-workload x every-implementation table")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     ap.add_argument("--profile-small", action="store_true",
@@ -766,6 +838,9 @@ def main(argv=None):
     prec = None
     if rank == 0 and world == 1 and not args.no_precision:
         prec = precision_leg()
+    table = None
+    if rank == 0 and world == 1 and not args.no_table:
+        table = baseline_table_leg(r)
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "chain-sweeps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -796,7 +871,8 @@ def main(argv=None):
                 "random_graph": graph,
                 "adaptive_ladder": ladder,
                 "workloads": wl,
-                "precision_error": prec}
+                "precision_error": prec,
+                "baseline_table": table}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

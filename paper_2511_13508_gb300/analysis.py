@@ -164,36 +164,64 @@ def overlap_distribution(qhist: np.ndarray, width: int = 10) -> np.ndarray:
     return coarse / np.where(tot > 0, tot, 1.0)
 
 
+def overlap_bin_width(qhist: np.ndarray) -> int:
+    """Fine bins per coarse bin for P(q) comparisons: about half the pooled standard deviation of q (so the
+    bulk of the distribution spans some eight coarse bins), between 1 and 10 fine bins of 0.01."""
+    h = np.asarray(qhist, np.float64).reshape(-1, np.asarray(qhist).shape[-1]).sum(0)
+    q = np.arange(h.size) / 100.0 - 1.0
+    sd = np.sqrt((h * q * q).sum() / max(h.sum(), 1.0))
+    return int(np.clip(round(sd / 0.02), 1, 10))
+
+
 def paired_difference(obs_a: dict, obs_b: dict, temps, N, pq_min_mass: float = 1e-3) -> dict:
     """Disorder-averaged difference a - b of the observables of two runs on the same disorder samples
     (paired over samples, e.g. FP32 against FP64): per temperature the jackknife mean and error of the
-    per-sample differences of E/N, C_V/N (Eq. (21)), <q^2>, <q^4> (Sec. IV.C), Y2, Y4 (Sec. IV.D), the scale
-    of each observable (the disorder average of run b) and z = difference / error; for P_J(q) on coarse bins
-    the same per (T, bin) where run b's mass is at least pq_min_mass."""
+    per-sample differences of E/N, C_V/N (Eq. (21)), <q^2>, <q^4> (Sec. IV.C), Y2, Y4 (Sec. IV.D), the
+    disorder average of run b and its own jackknife error (the statistical error of the observable), and
+    z = difference / error of the difference; for P_J(q) on coarse bins (overlap_bin_width) the same per
+    (T, bin) where run b's mass is at least pq_min_mass."""
     ta, tb = thermal_averages(obs_a, temps), thermal_averages(obs_b, temps)
     scale = {"E": 1.0 / N, "CV": 1.0 / N, "q2": 1.0, "q4": 1.0, "Y2": 1.0, "Y4": 1.0}
     out = {}
     for key, f in scale.items():
         d, err = jackknife(f * (ta[key] - tb[key]))
-        ref, _ = jackknife(f * tb[key])
+        ref, ref_err = jackknife(f * tb[key])
         with np.errstate(divide="ignore", invalid="ignore"):
             z = np.where(err > 0, d / err, 0.0)
-        out[key] = {"diff": d, "err": err, "ref": ref, "z": z}
-    pa, pb = overlap_distribution(obs_a["qhist"]), overlap_distribution(obs_b["qhist"])
+        out[key] = {"diff": d, "err": err, "ref": ref, "ref_err": ref_err, "z": z}
+    w = overlap_bin_width(obs_b["qhist"])
+    pa, pb = overlap_distribution(obs_a["qhist"], w), overlap_distribution(obs_b["qhist"], w)
     d, err = jackknife(pa - pb)
-    ref = pb.mean(0)
+    ref, ref_err = jackknife(pb)
     use = (ref >= pq_min_mass) & (err > 0)
     with np.errstate(divide="ignore", invalid="ignore"):
         z = np.where(use, d / np.where(err > 0, err, 1.0), 0.0)
-    out["Pq"] = {"diff": d, "err": err, "ref": ref, "z": z, "used": use}
+    out["Pq"] = {"diff": d, "err": err, "ref": ref, "ref_err": ref_err, "z": z, "used": use, "bin_width": w}
+    return out
+
+
+def within_statistical_error(diff: dict, k: float = 3.0) -> dict:
+    """Per observable of paired_difference: the fraction of temperatures (P(q): of used (T, bin) cells) where
+    |a - b| exceeds k times the statistical error of the difference of two independent runs, sqrt(2) times
+    the jackknife error of run b's disorder average, and the largest |a - b| in units of that error."""
+    out = {}
+    for key, v in diff.items():
+        d, e = np.abs(np.asarray(v["diff"])), np.sqrt(2.0) * np.asarray(v["ref_err"])
+        u = np.asarray(v["used"]) if key == "Pq" else np.ones(d.shape, bool)
+        u = u & (e > 0)
+        r = np.where(u, d / np.where(e > 0, e, 1.0), 0.0)
+        out[key] = {"frac_beyond": float((r[u] > k).mean()) if u.any() else 0.0,
+                    "max_in_sigma": float(r[u].max()) if u.any() else 0.0, "cells": int(u.sum())}
     return out
 
 
 def difference_summary(diff: dict) -> dict:
     """Per observable of paired_difference: the largest |difference| over temperatures (and its error), the
     mean over temperatures of |difference| / |disorder average| (P(q): of |difference| summed over bins), the
-    mean of z^2 (about 1 when the two runs sample the same law) and the largest |z|."""
+    mean of z^2 (about 1 when the two runs sample the same law), the largest |z|, and the largest |difference|
+    in units of the statistical error of the observable (within_statistical_error)."""
     out = {}
+    stat = within_statistical_error(diff)
     for key, v in diff.items():
         d, e, z = np.asarray(v["diff"]), np.asarray(v["err"]), np.asarray(v["z"])
         if key == "Pq":
@@ -201,12 +229,14 @@ def difference_summary(diff: dict) -> dict:
             out[key] = {"max_abs_diff": float(np.abs(d[u]).max()) if u.any() else 0.0,
                         "l1_diff_mean_over_T": float(np.abs(d).sum(-1).mean()),
                         "mean_z2": float((z[u] ** 2).mean()) if u.any() else 0.0,
-                        "max_abs_z": float(np.abs(z[u]).max()) if u.any() else 0.0, "bins_used": int(u.sum())}
+                        "max_abs_z": float(np.abs(z[u]).max()) if u.any() else 0.0, "bins_used": int(u.sum()),
+                        "bin_width": float(v["bin_width"]) / 100.0,
+                        "max_diff_in_stat_sigma": stat[key]["max_in_sigma"]}
             continue
         i = int(np.argmax(np.abs(d)))
         ref = np.abs(np.asarray(v["ref"]))
         rel = np.abs(d) / np.where(ref > 0, ref, np.inf)
         out[key] = {"max_abs_diff": float(abs(d[i])), "err_at_max": float(e[i]),
                     "mean_rel_diff": float(rel.mean()), "mean_z2": float((z ** 2).mean()),
-                    "max_abs_z": float(np.abs(z).max())}
+                    "max_abs_z": float(np.abs(z).max()), "max_diff_in_stat_sigma": stat[key]["max_in_sigma"]}
     return out

@@ -187,3 +187,21 @@ def test_paired_difference_z_of_independent_runs_is_standard():
     c = _synthetic_obs(np.random.default_rng(23), S, T, q_sd=0.38)
     d2 = analysis.paired_difference(c, b, np.linspace(0.5, 1.5, T), 16)
     assert np.abs(d2["q2"]["z"]).min() > 5
+
+
+def test_within_statistical_error_and_bin_width():
+    """Independent runs of one law differ by more than 3 sqrt(2) jackknife errors in about 0.3% of cells; a shift of
+    the overlap width is flagged; the coarse P(q) bins follow the spread of q (about half its standard deviation)."""
+    S, T = 16, 40
+    a = _synthetic_obs(np.random.default_rng(31), S, T)
+    b = _synthetic_obs(np.random.default_rng(32), S, T)
+    d = analysis.paired_difference(a, b, np.linspace(0.5, 1.5, T), 16)
+    st = analysis.within_statistical_error(d)
+    for key in ("E", "CV", "q2", "Y4", "Pq"):
+        assert st[key]["frac_beyond"] < 0.05, (key, st[key])
+    c = _synthetic_obs(np.random.default_rng(33), S, T, q_sd=0.38)
+    assert analysis.within_statistical_error(analysis.paired_difference(c, b, np.linspace(0.5, 1.5, T), 16))["q2"][
+        "frac_beyond"] == 1.0
+    assert analysis.overlap_bin_width(b["qhist"]) == 10        # sd 0.3 -> 15 fine bins, capped at 10
+    narrow = _synthetic_obs(np.random.default_rng(34), 2, 2, q_sd=0.04)
+    assert analysis.overlap_bin_width(narrow["qhist"]) == 2    # sd 0.04 -> 2 fine bins

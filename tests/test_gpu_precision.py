@@ -9,8 +9,10 @@ disorder-averaged difference FP32 - FP64 of E/N, C_V/N (Eq. (21)), <q^2>, <q^4> 
 (Sec. IV.D) and of P_J(q) on 20 coarse bins is compared with its jackknife error over samples (paired):
 the mean of z^2 over temperatures (bins) stays near 1 and no |z| is large.
 
-Shapes: N = 64 on 32 chains x 7 warps (the batched workload's shape), N = 128 and N = 256 on 8 chains x 11
-warps (packed FP32 blocks with the B_jk gather: the kernel family of the N = 256 benchmark).
+Shapes: N = 64 on 32 chains x 7 warps (the batched workload's shape) and N = 128 on 8 chains x 11 warps
+(packed FP32 blocks with the B_jk gather: the kernel family of the N = 256 benchmark; FP64 runs at N = 256
+take minutes on this GPU's FP64 units, and the N = 256 launch is checked update by update instead, in
+test_gpu_trace).
 """
 import numpy as np
 import pytest
@@ -51,17 +53,23 @@ CASES = [
     # N, samples, replicas, temperatures, burn-in, measured sweeps, FP32 block shape
     (64, 16, 2, 16, 1024, 8192, 32, 7),
     (128, 8, 2, 8, 512, 4096, 8, 11),
-    (256, 8, 2, 4, 256, 1536, 8, 11),
 ]
 
 
-@pytest.mark.parametrize("N,S,R,nT,burn,sweeps,cpb,cw", CASES, ids=["n64_32x7", "n128_8x11", "n256_8x11"])
+@pytest.mark.parametrize("N,S,R,nT,burn,sweeps,cpb,cw", CASES, ids=["n64_32x7", "n128_8x11"])
 def test_fp32_statistics_match_fp64(N, S, R, nT, burn, sweeps, cpb, cw):
     temps, d = paired_runs(N, S, R, nT, burn, sweeps, cpb, cw)
     summ = analysis.difference_summary(d)
     print("\nFP32 - FP64 at N=%d (%d samples x %d T x %d replicas, %d sweeps):" % (N, S, nT, R, sweeps))
     for key, v in summ.items():
         print("  %-3s %s" % (key, {k: (round(x, 6) if isinstance(x, float) else x) for k, x in v.items()}))
+    # the criterion of the precision pattern: FP32 agrees with FP64 within 3 statistical errors (jackknife
+    # over samples) per temperature and P(q) cell; a few per cent of cells may exceed it by chance
+    stat = analysis.within_statistical_error(d, 3.0)
+    for key, v in stat.items():
+        assert v["cells"] > 0, key
+        assert v["frac_beyond"] <= max(0.05, 1.5 / v["cells"]) and v["max_in_sigma"] < 5.0, (key, v)
+    # and the paired differences scatter like noise: no large systematic FP32 offset
     for key in ("E", "CV", "q2", "q4", "Y2", "Y4"):
         z = d[key]["z"]
         assert np.isfinite(z).all(), key
