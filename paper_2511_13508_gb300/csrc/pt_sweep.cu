@@ -528,6 +528,7 @@ template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
     b += (size_t)2 * G * sizeof(Proposal<real>) + 16;                     // proposals, double-buffered
     b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
     b += (size_t)(2 * 128 + 8) * sizeof(int);                             // bo / xtlo tables
+    b += (size_t)(maxN / 2) * sizeof(int);                                // pair sequence of a sweep
     b += 64;
     return b;
 }
@@ -575,11 +576,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     off += 129 * sizeof(int);
     int *s_unit = reinterpret_cast<int *>(smem + off);  // [0] group, [1] chunk, [2] abort
     volatile int *abort_flag = s_unit + 2;
+    int *s_pair = s_unit + 4;  // (j | k << 16) of every update of the current sweep
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const bool producer = (warp == NCW);
     const int c = lane % G, wq = lane / G;
-    const int worker = warp * WPW + wq;
+    // warp 0 also draws the proposals, so it takes the last workers of a chunk: it is the one left without a
+    // block when an update's last chunk is not full
+    const int worker = (warp == 0 ? NCW - 1 : warp - 1) * WPW + wq;
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
@@ -714,9 +718,17 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             const real cc = (real)prm.cc;
             for (int sw = sw0; sw < sw1; ++sw) {
                 const uint32_t sweep = (uint32_t)(sweep_base + sw);
+                // the sweep's pair sequence, drawn once per block (every warp has read the previous sweep's
+                // last entry before that update's barrier, which every thread here has passed)
+                for (int i = tid; i < N / 2; i += NCT) {
+                    int pj, pk;
+                    pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)i, N, pj, pk);
+                    s_pair[i] = pj | (pk << 16);
+                }
+                named_bar(1, NCT);
                 for (int u = 0; u < N / 2; ++u) {
-                    int j, k;
-                    pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
+                    const int jk = s_pair[u];
+                    const int j = jk & 0xffff, k = jk >> 16;
                     const Ranges Rg = update_ranges(sd, s_bo, mode_blk, j, k);
                     // proposal for chain c, drawn by warp 0 into the double-buffered table
                     Proposal<real> *Pp = prop + red_par * G;
