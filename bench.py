@@ -377,23 +377,27 @@ def run_gpu(args, rank, world, dist):
                 clocks=clocks, plain_rate=plain_rate, e2e=e2e, fl=fl, fl_exec=fl_exec)
 
 
-def learned_leg():
+def learned_leg(t_min=None, global_every=None, series=4096):
     """Effective samples/s at the coldest temperature, learned global move vs plain PT, on the learned-proposal
     workload (N=64, 16 samples x 32 T [0.3,1.6] x 2 replicas; 2^14 training configurations per sample from
-    the 8 coldest temperatures; a global move every 8 sweeps)."""
+    the 8 coldest temperatures; a global move every 8 sweeps).  t_min / global_every move the ladder's cold
+    end and the move's period (the colder leg: where plain PT is slow)."""
     import torch
     import paper_2511_13508_gb300 as pkg
     from paper_2511_13508_gb300 import gain, workload
     W = workload.workloads()["n64_learned"]
     nq = len(pkg.enumerate_quads(W.Ns[0]))
     Js = [workload.couplings(W.Ns[0], nq, s) for s in W.seeds]
-    pt = pkg.PT(W.Ns, Js, W.temps, W.replicas, 4401, precision="fp32", stream=torch.cuda.Stream(),
+    tmin = W.t_min if t_min is None else t_min
+    temps = workload.geometric_ladder(tmin, W.t_max, W.n_temps)
+    every = W.extra["global_every"] if global_every is None else global_every
+    pt = pkg.PT(W.Ns, Js, temps, W.replicas, 4401, precision="fp32", stream=torch.cuda.Stream(),
                 swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
-    r = gain.measure(pt, n_cold=W.extra["n_cold"], global_every=W.extra["global_every"],
-                     train_configs=W.extra["train_configs"], train_steps=6000)
+    r = gain.measure(pt, n_cold=W.extra["n_cold"], global_every=every,
+                     train_configs=W.extra["train_configs"], train_steps=6000, series=series)
     pt.close()
-    r["workload"] = "n64_learned: N=64, 16 samples x 32 T [0.3,1.6] x 2 replicas, FP32"
-    r["unit"] = "effective samples/s of E at the coldest T"
+    r["workload"] = "N=64 comb, 16 samples x 32 T [%g,%g] x 2 replicas, FP32" % (tmin, W.t_max)
+    r["unit"] = "effective samples/s of E (and of q^2) at the coldest T"
     return r
 
 
@@ -823,9 +827,10 @@ def main(argv=None):
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     r = run_gpu(args, rank, world, dist)
-    learned = None
+    learned = learned_cold = None
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg()
+        learned_cold = learned_leg(t_min=0.05, global_every=16, series=8192)
     graph = None
     if rank == 0 and world == 1 and not args.no_graph:
         graph = graph_leg()
@@ -868,6 +873,7 @@ def main(argv=None):
                 "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
                                    "speedup_fp32": r["value"] / world / r["plain_rate"]},
                 "learned_vs_plain": learned,
+                "learned_vs_plain_cold": learned_cold,
                 "random_graph": graph,
                 "adaptive_ladder": ladder,
                 "workloads": wl,

@@ -1,9 +1,13 @@
 """Effective independent samples per second at the coldest temperature, plain PT against PT with the
 learned global move (host orchestration of the library's calls; every step runs in its kernels).
 
-ESS/s = (series per ensemble) x sweeps/s / (2 tau_int(E) x sweeps between measurements), with tau_int from
-Sokal's automatic window over the running energy of the coldest temperature of every (sample, replica)
-ladder.  Sweep throughput is timed without host synchronisation; the energy series is read in between.
+ESS/s = (series per ensemble) x sweeps/s / (2 tau_int x sweeps between measurements), with tau_int from
+Sokal's automatic window, for two observables at the coldest temperature: the running energy of every
+(sample, replica) ladder, and the squared overlap q^2 of the first two replicas of every sample (Sec. IV.C;
+the slow modes of a glassy phase live in q).  Sweep throughput is timed without host synchronisation; the
+series are read in between.  The gain's error is a jackknife over disorder samples; the break-even acceptance
+is the global-move acceptance per round at which independent proposals every `global_every` sweeps would
+decorrelate as fast as plain PT does at the learned run's throughput (gain 1).
 """
 from __future__ import annotations
 
@@ -11,7 +15,7 @@ import time
 
 import numpy as np
 
-from . import stats
+from . import analysis, stats
 
 
 def _rate(pt, sweeps):
@@ -23,16 +27,23 @@ def _rate(pt, sweeps):
 
 
 def _series(pt, n, every):
-    out = np.zeros((n, pt.S, pt.R))
+    """Running energies [n, S, R] and q^2 of replicas 0 and 1 [n, S] at the coldest temperature."""
+    E = np.zeros((n, pt.S, pt.R))
+    q2 = np.zeros((n, pt.S))
+    N = int(pt.Ns[0])
     for i in range(n):
         pt.sweep(every)
-        out[i] = pt.running_energies().reshape(pt.S, pt.R, pt.nT)[:, :, 0]
-    return out
+        a, Ec = pt.state()
+        E[i] = Ec.reshape(pt.S, pt.R, pt.nT)[:, :, 0]
+        if pt.R >= 2:
+            a = a.reshape(pt.S, pt.R, pt.nT, N)
+            q2[i] = ((np.conj(a[:, 0, 0]) * a[:, 1, 0]).real.sum(-1) / N) ** 2
+    return E, q2
 
 
-def _ess_rate(pt, x, rate, every):
-    taus = np.array([stats.tau_int(x[:, s]) for s in range(pt.S)])  # per sample, replicas pooled
-    ess_per_sweep = pt.S * pt.R / (2.0 * taus.mean() * every)
+def _ess_rate(pt, x, rate, every, series_per_sample):
+    taus = np.array([stats.tau_int(x[:, s]) for s in range(pt.S)])  # per sample (replicas pooled for E)
+    ess_per_sweep = pt.S * series_per_sample / (2.0 * taus.mean() * every)
     return taus, ess_per_sweep * rate
 
 
@@ -41,8 +52,9 @@ def measure(pt, *, n_cold, global_every, train_configs, train_steps, lr=1e-3, ba
     """Runs plain PT, then trains the proposal on the same ensemble and runs PT with global moves."""
     pt.sweep(burn_in)
     rate0 = _rate(pt, rate_sweeps)
-    x0 = _series(pt, series, every)
-    tau0, ess0 = _ess_rate(pt, x0, rate0, every)
+    x0, q0 = _series(pt, series, every)
+    tau0, ess0 = _ess_rate(pt, x0, rate0, every, pt.R)
+    tq0, essq0 = _ess_rate(pt, q0, rate0, every, 1)
     t0 = time.perf_counter()
     pt.learn_init(n_cold=n_cold, batch=batch, data_per_sample=train_configs, seed=seed)
     rounds = train_configs // (n_cold * pt.R)
@@ -54,13 +66,26 @@ def measure(pt, *, n_cold, global_every, train_configs, train_steps, lr=1e-3, ba
     pt.sweep(max(burn_in // 4, global_every))
     rate1 = _rate(pt, rate_sweeps)
     pt.reset_observables()
-    x1 = _series(pt, series, every)
+    x1, q1 = _series(pt, series, every)
     o = pt.observables()
     acc = o["gm_acc"].sum(0)[:n_cold] / np.maximum(o["gm_att"].sum(0)[:n_cold], 1)
-    tau1, ess1 = _ess_rate(pt, x1, rate1, every)
+    tau1, ess1 = _ess_rate(pt, x1, rate1, every, pt.R)
+    tq1, essq1 = _ess_rate(pt, q1, rate1, every, 1)
+    # the gain is a ratio of mean autocorrelation times over the same disorder samples: jackknife over samples
+    ratio = lambda a, b: a.mean(0) / b.mean(0)
+    _, gE_err = analysis.jackknife((tau0, tau1), ratio)
+    _, gq_err = analysis.jackknife((tq0, tq1), ratio)
+    acc_mean = float(np.mean(acc))
     return {
         "ess_per_s_plain": ess0, "ess_per_s_learned": ess1, "gain": ess1 / ess0,
+        "gain_err": float(gE_err) * rate1 / rate0,
+        "break_even_acceptance": float(global_every / (tau0.mean() * every * rate1 / rate0)),
+        "acceptance_mean": acc_mean,
         "tau_int_sweeps_plain": float(tau0.mean() * every), "tau_int_sweeps_learned": float(tau1.mean() * every),
+        "q2": {"ess_per_s_plain": essq0, "ess_per_s_learned": essq1, "gain": essq1 / essq0,
+               "gain_err": float(gq_err) * rate1 / rate0,
+               "tau_int_sweeps_plain": float(tq0.mean() * every), "tau_int_sweeps_learned": float(tq1.mean() * every),
+               "mean_plain": float(q0.mean()), "mean_learned": float(q1.mean())},
         "sweeps_per_s_plain": rate0, "sweeps_per_s_learned": rate1,
         "acceptance_coldest": [float(v) for v in acc], "train_seconds": t_train, "train_steps": train_steps,
         "train_configs_per_sample": rounds * n_cold * pt.R,

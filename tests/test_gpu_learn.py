@@ -472,3 +472,14 @@ def test_gain_measurement_reports_ess_of_both_methods():
     assert r["nll_last"] < r["nll_first"]
     assert max(r["acceptance_coldest"]) > 0.01
     assert abs(r["mean_E_coldest_plain"] - r["mean_E_coldest_learned"]) < 0.05 * abs(r["mean_E_coldest_plain"])
+    # the gain is the ESS ratio, i.e. the ratio of autocorrelation times times the throughput ratio, with a
+    # finite jackknife error; the same for q^2
+    g = (r["tau_int_sweeps_plain"] / r["tau_int_sweeps_learned"]) * (r["sweeps_per_s_learned"] / r["sweeps_per_s_plain"])
+    assert r["gain"] == pytest.approx(g, rel=1e-9)
+    assert np.isfinite(r["gain_err"]) and r["gain_err"] > 0
+    assert r["q2"]["gain"] > 0 and np.isfinite(r["q2"]["gain_err"])
+    assert abs(r["q2"]["mean_plain"] - r["q2"]["mean_learned"]) < 0.25 * r["q2"]["mean_plain"]
+    # a gain needs the acceptance to beat the break-even one: below it, no gain beyond the measurement error
+    assert r["break_even_acceptance"] > 0
+    if r["acceptance_mean"] < 0.5 * r["break_even_acceptance"]:
+        assert r["gain"] < 1.0 + 3.0 * r["gain_err"], r
