@@ -377,7 +377,7 @@ def run_gpu(args, rank, world, dist):
                 clocks=clocks, plain_rate=plain_rate, e2e=e2e, fl=fl, fl_exec=fl_exec)
 
 
-def learned_leg(t_min=None, global_every=None, series=4096):
+def learned_leg(t_min=None, global_every=None, series=4096, burn_in=4096):
     """Effective samples/s at the coldest temperature, learned global move vs plain PT, on the learned-proposal
     workload (N=64, 16 samples x 32 T [0.3,1.6] x 2 replicas; 2^14 training configurations per sample from
     the 8 coldest temperatures; a global move every 8 sweeps).  t_min / global_every move the ladder's cold
@@ -394,7 +394,7 @@ def learned_leg(t_min=None, global_every=None, series=4096):
     pt = pkg.PT(W.Ns, Js, temps, W.replicas, 4401, precision="fp32", stream=torch.cuda.Stream(),
                 swap_every=W.swap_every, measure_every=W.measure_every, resync_every=W.resync_every)
     r = gain.measure(pt, n_cold=W.extra["n_cold"], global_every=every,
-                     train_configs=W.extra["train_configs"], train_steps=6000, series=series)
+                     train_configs=W.extra["train_configs"], train_steps=6000, series=series, burn_in=burn_in)
     pt.close()
     r["workload"] = "N=64 comb, 16 samples x 32 T [%g,%g] x 2 replicas, FP32" % (tmin, W.t_max)
     r["unit"] = "effective samples/s of E (and of q^2) at the coldest T"
@@ -830,7 +830,7 @@ def main(argv=None):
     learned = learned_cold = None
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg()
-        learned_cold = learned_leg(t_min=0.05, global_every=16, series=8192)
+        learned_cold = learned_leg(t_min=0.05, global_every=16, series=8192, burn_in=1 << 15)
     graph = None
     if rank == 0 and world == 1 and not args.no_graph:
         graph = graph_leg()

@@ -96,7 +96,8 @@ def measure(pt, *, n_cold, global_every, train_configs, train_steps, lr=1e-3, ba
         "tau_int_sweeps_plain": float(tau0.mean() * every), "tau_int_sweeps_learned": float(tau1.mean() * every),
         "tau_int_sweeps_plain_before_after": [float(np.mean([stats.tau_int(x0a[:, s]) for s in range(pt.S)]) * every),
                                               float(np.mean([stats.tau_int(x0b[:, s]) for s in range(pt.S)]) * every)],
-        "plain_drift_E": {"after_minus_before": float(dE), "err": float(dE_err)},
+        "plain_drift_E": {"after_minus_before": float(dE), "err": float(dE_err),
+                          "significant": bool(abs(dE) > 3.0 * dE_err)},
         "q2": {"ess_per_s_plain": essq0, "ess_per_s_learned": essq1, "gain": essq1 / essq0,
                "gain_err": float(gq_err) * rate1 / rate0,
                "tau_int_sweeps_plain": float(tq0.mean() * every), "tau_int_sweeps_learned": float(tq1.mean() * every),
