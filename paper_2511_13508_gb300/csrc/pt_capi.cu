@@ -929,9 +929,9 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     const int chains_ps = replicas * n_T;
     // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
     // N >= 128: 8 chains x 11 warps; 48 <= N < 128: the most chains per block (32, 16, 8) that still give
-    // about one group per SM (N = 64: 32 x 7 for 64 samples x 64 chains, 19.6M chain-sweeps/s, against
-    // 11.3M with 8 x 11; but 8 x 11 for 16 samples x 64 chains, 9.3k sweeps/s against 4.9k with 32 x 7, which
-    // leaves most SMs idle), 32 x 7 when none does; N < 48: 16 x 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3
+    // about one group per SM (N = 64: 32 x 11 for 64 samples x 64 chains, 22.3M chain-sweeps/s, against
+    // 11.9M with 8 x 11; but 8 x 11 for 16 samples x 64 chains, 10.0M against 5.7M with 32 x 11, which
+    // leaves most SMs idle), 32 x 11 when none does; N < 48: 16 x 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3
     int G = cfg.chains_per_block, ncw = 0;
     if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
     if (G == 0) {
@@ -950,8 +950,10 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         }
         if (G > 8 && chains_ps <= 8) G = 8;
     }
+    // FP32 field warps: 11 from N = 48 on (N = 64, 64 samples: 32 x 11 22.3M chain-sweeps/s against 21.6M with
+    // 32 x 7; ragged batch: 16 x 11 8.24M against 7.53M with 16 x 7), else 7
     if (c->dbl) ncw = (G == 16) ? 3 : 7;
-    else ncw = (G == 8) ? (c->maxN >= 48 ? 11 : 7) : 7;
+    else ncw = (c->maxN >= 48) ? 11 : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !c->gfp32 && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;
@@ -1499,7 +1501,7 @@ int pt_autotune(pt_ctx *c, int trial_sweeps, int *chosen) {
     struct Cand { int G, ncw, spu; };
     std::vector<Cand> cands;
     const int Gs_f[] = {8, 16, 32}, Gs_d[] = {8, 16};
-    const int ncws[] = {3, 7, 11, 15};
+    const int ncws[] = {3, 7, 9, 11, 15};
     for (int G : (c->dbl ? std::vector<int>(Gs_d, Gs_d + 2) : std::vector<int>(Gs_f, Gs_f + 3))) {
         if (G > 8 && cps < G / 2) continue;  // mostly empty blocks
         for (int n : ncws)

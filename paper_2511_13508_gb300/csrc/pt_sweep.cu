@@ -1100,7 +1100,7 @@ static int occupancy_t(int maxN) {
     X(float, 8, 12) X(float, 8, 13) X(float, 8, 14) \
     X(float, 16, 14) X(float, 32, 14) X(float, 16, 15) \
     X(float, 16, 7) X(float, 16, 11)                \
-    X(float, 32, 3) X(float, 32, 7)                 \
+    X(float, 32, 3) X(float, 32, 7) X(float, 32, 9) X(float, 32, 11) \
     X(double, 8, 7) X(double, 16, 3)
 
 bool sweep_variant_exists(bool dbl, int G, int ncw) {

@@ -16,11 +16,11 @@ parallel Delta E, cross term of reading R5):
   - beta and, for FP64, the running energy against H(state).
 
 Shapes: the N = 256 bench launch (16 samples x 48 T x 2 replicas, 8 chains x 11 field warps, packed FP32
-blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 96 on the default
-16-chain scalar shape, N = 64 on 32 x 7, N = 48 on 8 chains (packed, B picked out of the blocks), N = 16
-(16 x 7), N = 24 on 8 x 7 (packed), a ragged batch mixing the gathered and picked-out variants in one
-launch, and the FP64 kernels.  Updates include the first and last of a sweep and pairs at the ends of the mode range, adjacent pairs
-and j + k = N - 1.
+blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 96 on its 16-chain
+default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
+out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, ragged batches with the default and the autotuned shape
+(mixing the gathered and picked-out variants in one launch), and the FP64 kernels.  Updates include the first
+and last of a sweep and pairs at the ends of the mode range, adjacent pairs and j + k = N - 1.
 """
 import numpy as np
 import pytest
@@ -209,6 +209,8 @@ CASES = [
     ("n96_8x11_gatherB", [96, 96], 2, 5, "fp32", 8, 11),
     ("n96_default_16chains", [96, 96], 2, 8, "fp32", 0, 0),
     ("n64_32x7", [64, 64], 2, 16, "fp32", 32, 7),
+    ("n64_default_32x11", [64, 64], 2, 16, "fp32", 0, 0),
+    ("n64_16x11", [64, 64], 2, 8, "fp32", 16, 11),
     ("n48_8chains_packed", [48, 48, 48], 2, 5, "fp32", 8, 0),
     ("n16_16x7", [16, 16], 2, 8, "fp32", 0, 0),
     ("n24_8x7_packed", [24, 24], 2, 4, "fp32", 0, 0),
