@@ -106,3 +106,82 @@ def test_autotune_keeps_the_ensemble_and_picks_a_valid_shape():
     b.load(blob)
     b.sweep(24)
     assert np.array_equal(a.state()[0], b.state()[0])
+
+
+def _oracle_blocks(args):
+    """One disorder sample on the oracle (spawned process): burn-in, then per block of sweeps the observables."""
+    import os, sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle as orc
+    N, J, temps, R, seed, burn, nb, sw = args
+    pt = orc.OraclePT([N], [J], temps, R, seed, swap_every=64, measure_every=4, resync_every=64)
+    pt.sweep(burn)
+    out = []
+    for _ in range(nb):
+        pt.reset_observables()
+        pt.sweep(sw)
+        o = pt.observables()
+        out.append((o["stat"][0], o["qstat"][0], o["qhist"][0]))
+    return out
+
+
+def _block_observables(blocks, temps, N):
+    """Per block [nb, S, T]: E/N, C_V/N, <q^2>, Y2, Y4 and P(q) on coarse bins of width 0.1 [nb, S, T, 20]."""
+    from paper_2511_13508_gb300 import analysis
+    res = []
+    for st, qs, qh in blocks:
+        ta = analysis.thermal_averages({"stat": st, "qstat": qs}, temps)
+        obs = np.stack([ta["E"] / N, ta["CV"] / N, ta["q2"], ta["Y2"], ta["Y4"]], -1)
+        res.append((obs, analysis.overlap_distribution(qh, 10)))
+    return np.array([r[0] for r in res]), np.array([r[1] for r in res])
+
+
+N64 = dict(N=64, S=4, R=2, nT=8, burn=1024, nb=16, sw=256)
+
+
+@pytest.fixture(scope="module")
+def oracle_n64_blocks():
+    """The oracle's block observables for the N = 64 long-run comparison (one spawned process per sample)."""
+    import multiprocessing as mp
+    N, S, R, nT, burn, nb, sw = (N64[k] for k in ("N", "S", "R", "nT", "burn", "nb", "sw"))
+    temps = workload.geometric_ladder(0.3, 1.6, nT)
+    Js = couplings([N] * S, 8100)
+    with mp.get_context("spawn").Pool(S) as pool:
+        per_sample = pool.map(_oracle_blocks, [(N, Js[s], temps, R, 500 + s, burn, nb, sw) for s in range(S)])
+    return [(np.stack([per_sample[s][b][0] for s in range(S)]), np.stack([per_sample[s][b][1] for s in range(S)]),
+             np.stack([per_sample[s][b][2] for s in range(S)])) for b in range(nb)]
+
+
+@pytest.mark.parametrize("cpb,cw", [(32, 11), (16, 11)])
+def test_fp32_long_run_matches_oracle_at_n64_production_shapes(cpb, cw, oracle_n64_blocks):
+    """N = 64 on the batched workload's block shapes (32 x 11, 16 x 11: packed FP32 blocks, B picked out of the
+    blocks): independent FP32 GPU and FP64 oracle runs on the same couplings; per (sample, T) block means of
+    E/N, C_V/N (Eq. (21)), <q^2> (Sec. IV.C), Y2 and Y4 (Sec. IV.D), and P(q) per T pooled over samples, agree
+    within their block errors."""
+    N, S, R, nT, burn, nb, sw = (N64[k] for k in ("N", "S", "R", "nT", "burn", "nb", "sw"))
+    temps = workload.geometric_ladder(0.3, 1.6, nT)
+    Js = couplings([N] * S, 8100)
+    gpu = pkg.PT([N] * S, Js, temps, R, 71, precision="fp32", chains_per_block=cpb, consumer_warps=cw,
+                 swap_every=64, measure_every=4, resync_every=64)
+    gpu.sweep(burn)
+    gblocks = []
+    for _ in range(nb):
+        gpu.reset_observables()
+        gpu.sweep(sw)
+        o = gpu.observables()
+        gblocks.append((o["stat"], o["qstat"], o["qhist"]))
+    g, gp = _block_observables(gblocks, temps, N)
+    o, op = _block_observables(oracle_n64_blocks, temps, N)
+    se = np.sqrt(g.var(0, ddof=1) / nb + o.var(0, ddof=1) / nb) + 1e-15
+    z = (g.mean(0) - o.mean(0)) / se          # [S, T, 5]
+    print("\nN=64 %dx%d vs oracle: max |z| %.2f, mean z^2 %.2f" % (cpb, cw, np.abs(z).max(), (z ** 2).mean()))
+    assert np.mean(np.abs(z) > 3.0) < 0.05, np.round(z, 2)
+    assert np.abs(z).max() < 5.0 and np.mean(z ** 2) < 2.0
+    # P(q) per temperature pooled over samples, on coarse bins holding at least 1% of the mass
+    gq, oq = gp.mean(1), op.mean(1)           # [nb, T, 20]
+    use = oq.mean(0) >= 0.01
+    seq = np.sqrt(gq.var(0, ddof=1) / nb + oq.var(0, ddof=1) / nb) + 1e-15
+    zq = ((gq.mean(0) - oq.mean(0)) / seq)[use]
+    print("P(q): %d cells, max |z| %.2f, mean z^2 %.2f" % (zq.size, np.abs(zq).max(), (zq ** 2).mean()))
+    assert zq.size >= 2 * nT
+    assert np.abs(zq).max() < 5.0 and np.mean(zq ** 2) < 2.0
