@@ -193,8 +193,12 @@ int pt_fields(pt_ctx *ctx, int sample, int j, int k, double *out);
  *       update, and 1.0 for a written record (0.0 everywhere for chains that were not traced);
  *   a   optional (NULL = not wanted), state layout of pt_get_state: every traced chain's amplitudes just
  *       before the update, in the kernel's precision widened to double.
+ * Contexts of pt_create_graph (the FP32 quadruplet-list kernels) reduce the j-k cross term for the kernel's
+ * own proposal instead of B_jk and A_jk: there fields 6..9 hold Re sum_{q holding j and k} J_q (product of
+ * the other two factors) dx_j dx_k (dx = conj(d) at positions 0 and 3, d at 1 and 2; the energy change is
+ * then -cc Re[conj(dj) h_j + conj(dk) h_k] - cc * field 6) and three zeros.
  * Caller-owned host buffers; the call synchronises the context's stream.  PT_EINVAL for an update outside
- * [0, max N/2); PT_EUNSUPPORTED for the quadruplet-list paths (PT_PREC_FP64_PLAIN, pt_create_graph). */
+ * [0, max N/2); PT_EUNSUPPORTED for PT_PREC_FP64_PLAIN. */
 #define PT_TRACE_REC 20
 int pt_trace_update(pt_ctx *ctx, int update, double *rec, double *a);
 

@@ -292,6 +292,7 @@ GraphParams graph_params(pt_ctx *c) {
     p.R = c->R; p.nT = c->nT; p.maxN = c->maxN; p.seed = c->seed; p.cc = c->cfg.cc_factor; p.ctl = c->d_ctl;
     p.measure_every = c->cfg.measure_every; p.snap_a = reinterpret_cast<float2 *>(c->d_snap_a);
     p.snap_E = c->d_snap_E; p.n_snap_max = c->n_snap_max; p.a_total = c->a_total; p.n_chains = c->n_chains;
+    p.trace = c->d_trace;
     return p;
 }
 
@@ -1031,7 +1032,7 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     RC(dalloc(c, &c->d_stat, (size_t)S * n_T * PT_NSTAT));
     RC(dalloc(c, &c->d_qstat, (size_t)S * n_T * PT_NQSTAT));
     RC(dalloc(c, &c->d_fields, (size_t)chains_ps * 8));
-    if (!c->plain && !c->gfp32) RC(dalloc(c, &c->d_trace, (size_t)c->n_chains * kTraceRec + (size_t)c->a_total * 2));
+    if (!c->plain) RC(dalloc(c, &c->d_trace, (size_t)c->n_chains * kTraceRec + (size_t)c->a_total * 2));
     RC(dalloc(c, &c->d_ctl, 1));
 
     // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
@@ -1364,7 +1365,7 @@ int pt_fields(pt_ctx *c, int sample, int j, int k, double *out) {
 
 int pt_trace_update(pt_ctx *c, int update, double *rec, double *a) {
     if (!c || !rec) return fail(c, PT_EINVAL, "pt_trace_update: NULL argument");
-    if (!c->d_trace) return fail(c, PT_EUNSUPPORTED, "pt_trace_update: not available for the quadruplet-list paths");
+    if (!c->d_trace) return fail(c, PT_EUNSUPPORTED, "pt_trace_update: not available for PT_PREC_FP64_PLAIN");
     if (update < 0 || update >= c->maxN / 2) return fail(c, PT_EINVAL, "pt_trace_update: update must be in [0, maxN/2)");
     int rc = watchdog_sync(c);
     if (rc != PT_OK) return rc;

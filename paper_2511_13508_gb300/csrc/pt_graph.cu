@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
     const float *recJ = p.recJ + sd.inc_off;
     const float cc_f = (float)p.cc;
     const long long base = p.ctl->sweep_base;
+    // update trace: absolute sweep + 1 and update to record (0 = none)
+    const long long tr_at = p.trace ? p.ctl->trace_at : 0ll;
+    const int tr_u = p.trace ? p.ctl->trace_update : -1;
     __syncthreads();
     // kFew: the pair of the next update and this worker's record of it
     int jn = 0, kn = 0;
@@ -241,7 +244,24 @@ __global__ void __launch_bounds__(kGThreads) graph_sweep_kernel(GraphParams p) {
                 // Re(conj(d) h) = d.x h.x + d.y h.y
                 const float dH = -cc_f * (P.dj.x * t[0] + P.dj.y * t[1] + P.dk.x * t[2] + P.dk.y * t[3] + t[4]);
                 ++att;
-                if (dH <= 0.f || P.U < expf(-beta * dH)) {
+                const bool accept = dH <= 0.f || P.U < expf(-beta * dH);
+                if (tr_at == base + sw + 1 && u == tr_u) {
+                    // the record of this update and the chain's state before it (this leader is the only writer
+                    // of its chain's column, so the table still holds the old a_j, a_k)
+                    double *rec_o = p.trace + (int64_t)cid * kTraceRec;
+                    const double v[kTraceRec] = {(double)j, (double)k, (double)t[0], (double)t[1], (double)t[2],
+                                                 (double)t[3], (double)t[4], 0.0, 0.0, 0.0, (double)P.nj.x,
+                                                 (double)P.nj.y, (double)P.nk.x, (double)P.nk.y, (double)P.U,
+                                                 (double)dH, accept ? 1.0 : 0.0, (double)beta, E, 1.0};
+                    for (int e = 0; e < kTraceRec; ++e) rec_o[e] = v[e];
+                    double2 *st_o = reinterpret_cast<double2 *>(p.trace + (int64_t)p.n_chains * kTraceRec) + sd.a_off +
+                                    (int64_t)(cid - (uint32_t)sd.chain0) * N;
+                    for (int x = 0; x < N; ++x) {
+                        const float2 a = ga[x * kGRS + c];
+                        st_o[x] = make_double2((double)a.x, (double)a.y);
+                    }
+                }
+                if (accept) {
                     ga[j * kGRS + c] = P.nj;
                     ga[k * kGRS + c] = P.nk;
                     E += (double)dH;

@@ -155,6 +155,7 @@ struct GraphParams {
     int n_chains;
     int renorm;              // energy kernel: rescale to sum |a|^4 = N first
     double *E_out, *E_state; // energy kernel outputs (optional)
+    double *trace;           // sweep kernel: update trace (as SweepParams::trace; the cross term in place of B, A)
 };
 cudaError_t launch_wait_probe(Control *ctl, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_graph_sweep(const GraphParams &p, int n_groups, cudaStream_t s);

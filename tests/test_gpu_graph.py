@@ -209,3 +209,86 @@ def test_fp32_graph_variants_keep_energies_and_constraint(N):
     Eo = [oracle.energy(N, graphs[0], Js[0], x) for x in xs]
     assert np.allclose(E1, Eo, rtol=1e-4, atol=1e-3), np.abs(np.asarray(E1) - Eo).max()
     assert np.allclose([(np.abs(x) ** 4).sum() / len(x) for x in xs], 1.0, rtol=1e-4)
+
+
+def _rss(q, J, x, modes):
+    """Root sum of squares of the terms of the quadruplets holding every mode in `modes`."""
+    m = np.ones(len(q), bool)
+    for l in modes:
+        m &= (q == l).any(1)
+    mag = np.abs(x)[q[m]]
+    for l in modes:
+        mag = np.where(q[m] == l, 1.0, mag)
+    return float(np.sqrt(((np.abs(J[m]) * mag.prod(1)) ** 2).sum()))
+
+
+@pytest.mark.parametrize("kind", ["random_n64", "random_ragged", "sparse_n512"])
+def test_graph_kernel_trace_matches_oracle(kind):
+    """The FP32 group kernels traced update by update (pt_trace_update): per chain the kernel's h_j, h_k against
+    the oracle's fields, its j-k cross term for its own proposal against the oracle's bilinear terms, its proposal
+    and Delta H against or_propose / or_delta_h on the same state, and its decision (Sec. III.A.1, III.A.3),
+    within 1e-5 of each magnitude.  Covers the staged (dense) and few-record (sparse) kernel variants."""
+    if kind == "random_n64":
+        Ns, R, nT = [64, 64], 2, 4
+        graphs, Js = _graphs(Ns, 900)
+    elif kind == "random_ragged":
+        Ns, R, nT = [48, 24, 32], 2, 3
+        graphs, Js = _graphs(Ns, 910)
+    else:
+        Ns, R, nT = [512, 512], 2, 4
+        graphs = [workload.sparse_comb_graph(512, 16, 920 + s) for s in range(2)]
+        Js = [workload.couplings(512, len(g), 930 + s) * 512 for s, g in enumerate(graphs)]
+    temps = workload.geometric_ladder(0.3, 1.6, nT)
+    seed = 55
+    pt = pkg.PT(Ns, Js, temps, R, seed, precision="fp32", graphs=graphs, swap_every=8, measure_every=4,
+                resync_every=16)
+    pt.sweep(9)
+    cps = R * nT
+    offs = np.concatenate([[0], np.cumsum([n for n in Ns for _ in range(cps)])])
+    rng = np.random.default_rng(3)
+    checked = amb = 0
+    tol = 1e-5
+    for call in range(4):
+        sweep = pt.counters[0]
+        u = [0, max(Ns) // 2 - 1, 5, 11][call] % (max(Ns) // 2)
+        rec, a = pt.trace_update(u)
+        for ci in rng.choice(len(rec), size=min(len(rec), 12), replace=False):
+            s, t = ci // cps, ci % nT
+            N, q, J = Ns[s], graphs[s], Js[s]
+            if u >= N // 2:
+                assert rec[ci, 19] == 0.0
+                continue
+            r_ = rec[ci]
+            assert r_[19] == 1.0
+            j, k = int(r_[0]), int(r_[1])
+            assert (j, k) == oracle.pair(seed, s, sweep, u, N)
+            x = a[offs[ci]:offs[ci] + N]
+            hj, hk = complex(r_[2], r_[3]), complex(r_[4], r_[5])
+            hj_o, hk_o = oracle.field(N, q, J, x, j), oracle.field(N, q, J, x, k)
+            sj, sk, sjk = _rss(q, J, x, [j]), _rss(q, J, x, [k]), _rss(q, J, x, [j, k])
+            assert abs(hj - hj_o) <= tol * max(abs(hj_o), sj, 1e-30), (ci, hj, hj_o)
+            assert abs(hk - hk_o) <= tol * max(abs(hk_o), sk, 1e-30), (ci, hk, hk_o)
+            nj, nk, U = complex(r_[10], r_[11]), complex(r_[12], r_[13]), r_[14]
+            nj_o, nk_o, U_o = oracle.propose(seed, ci, sweep, u, x, j, k)
+            K2 = (abs(x[j]) ** 4 + abs(x[k]) ** 4) ** 0.5
+            for n_, o_ in ((nj, nj_o), (nk, nk_o)):
+                assert abs(abs(n_) ** 2 - abs(o_) ** 2) <= 1e-6 * K2
+            assert abs(U - U_o) <= 1e-7
+            dj, dk = nj - x[j], nk - x[k]
+            B_o, A_o = oracle.cross_terms(N, q, J, x, j, k)
+            cross_o = (np.conj(dj) * dk * B_o + np.conj(dj) * np.conj(dk) * A_o).real
+            cscale = abs(dj) * abs(dk) * sjk
+            assert abs(r_[6] - cross_o) <= tol * max(abs(cross_o), cscale) + 1e-30, (ci, r_[6], cross_o)
+            assert r_[7] == 0.0 and r_[8] == 0.0 and r_[9] == 0.0
+            dH, acc, beta = r_[15], r_[16], r_[17]
+            dH_o = oracle.delta_h(N, q, J, x, j, k, nj, nk)
+            dscale = abs(dj) * sj + abs(dk) * sk + cscale
+            assert abs(dH - dH_o) <= tol * max(abs(dH_o), dscale), (ci, dH, dH_o)
+            assert beta == pytest.approx(1.0 / temps[t], rel=1e-7)
+            margin = 4 * tol * max(abs(dH_o), dscale)
+            if abs(dH_o) <= margin or abs(-np.log(U_o) / beta - dH_o) <= margin:
+                amb += 1
+            else:
+                assert bool(acc) == (dH_o <= 0.0 or U_o < np.exp(-beta * dH_o)), (ci, dH, dH_o, U)
+            checked += 1
+    assert checked > 0 and amb <= max(1, checked // 20)
