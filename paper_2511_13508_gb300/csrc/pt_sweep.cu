@@ -540,6 +540,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS, NW = Sh::NW;
     constexpr int BT = (256 + NW - 1) / NW < 8 ? (256 + NW - 1) / NW : 8;  // B couplings held per lane
     constexpr int NCT = NCW * 32;  // consumer threads
+    constexpr bool kOneDecider = G >= 16;  // one warp reduces and decides (see the update's decision step)
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -802,17 +803,40 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     for (int o = G; o < 32; o <<= 1)
 #pragma unroll
                         for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
-                    // layout [e][warp][chain]: the 8 chains of one (e, warp) are consecutive words, so both the
-                    // stores below and the reads after the barrier (32 lanes = 4 warps x 8 chains) are free of
-                    // bank conflicts
                     real *rb = red + (size_t)red_par * NCW * G * 8;
-                    if (wq == 0) {
+                    if constexpr (Sh::PACKED) {
+                        // layout [half][warp][chain] of float4: the chains of one (half, warp) are consecutive, so
+                        // the stores and the reads after the barrier are free of bank conflicts
+                        float4 *rb4 = reinterpret_cast<float4 *>(rb);
+                        if (wq == 0) {
+                            rb4[(0 * NCW + warp) * G + c] = make_float4(v[0], v[1], v[2], v[3]);
+                            rb4[(1 * NCW + warp) * G + c] = make_float4(v[4], v[5], v[6], v[7]);
+                        }
+                    } else {
+                        // layout [e][warp][chain]: the 8 chains of one (e, warp) are consecutive words, so both the
+                        // stores below and the reads after the barrier (32 lanes = 4 warps x 8 chains) are free of
+                        // bank conflicts
+                        if (wq == 0) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) rb[(e * NCW + warp) * G + c] = v[e];
+                            for (int e = 0; e < 8; ++e) rb[(e * NCW + warp) * G + c] = v[e];
+                        }
+                    }
+                    // packed: the neighbours of j and k for the window rows rewritten on acceptance (modes other
+                    // than j and k keep their values during this update)
+                    float2 nb[4];
+                    if (Sh::PACKED && (!kOneDecider || warp == 0)) {
+                        const float2 *asf = reinterpret_cast<const float2 *>(as);
+                        nb[0] = asf[(j - 1 + APAD) * RS + c]; nb[1] = asf[(j + 1 + APAD) * RS + c];
+                        nb[2] = asf[(k - 1 + APAD) * RS + c]; nb[3] = asf[(k + 1 + APAD) * RS + c];
                     }
                     named_bar(1, NCT);
-                    {
-                        // every warp forms the same totals (fixed order) and takes the same decision
+                    // 16 and 32 chains per block: warp 0 alone forms the totals, takes the decision and writes the
+                    // new amplitudes, windows, energies and counters, and a second barrier orders those writes
+                    // before every warp's next update (every other warp would repeat the same reads of all
+                    // partial sums: NCW x G x 8 words each).  8 chains per block: every warp forms the same totals
+                    // in the same order, takes the same decision and writes the same values, with no second
+                    // barrier (measured faster at N = 256).
+                    if (!kOneDecider || warp == 0) {
                         // lane (c, wq) adds the partials of warps wq, wq + WPW, ...: the trip count is the
                         // same on every lane (predicated body), so the warp is converged at the shuffles
                         real t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -820,8 +844,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                         for (int w0 = 0; w0 < NCW; w0 += WPW) {
                             const int w = w0 + wq;
                             if (w < NCW) {
+                                if constexpr (Sh::PACKED) {
+                                    const float4 *rb4 = reinterpret_cast<const float4 *>(rb);
+                                    const float4 lo = rb4[(0 * NCW + w) * G + c], hi = rb4[(1 * NCW + w) * G + c];
+                                    t[0] += lo.x; t[1] += lo.y; t[2] += lo.z; t[3] += lo.w;
+                                    t[4] += hi.x; t[5] += hi.y; t[6] += hi.z; t[7] += hi.w;
+                                } else {
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) t[e] += rb[(e * NCW + w) * G + c];
+                                    for (int e = 0; e < 8; ++e) t[e] += rb[(e * NCW + w) * G + c];
+                                }
                             }
                         }
                         __syncwarp();
@@ -843,13 +874,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                                 as[(j + APAD) * RS + c] = P.nj;
                                 as[(k + APAD) * RS + c] = P.nk;
                                 if constexpr (Sh::PACKED) {
-                                    // every warp writes the same values, after its own writes of a_j and a_k
-                                    const float2 *asf = reinterpret_cast<const float2 *>(as);
-                                    const int rows = N + 2 * APAD;
-                                    packed_rows<RS>(asf, awin, G, j - 1 + APAD, rows, c);
-                                    packed_rows<RS>(asf, awin, G, j + APAD, rows, c);
-                                    packed_rows<RS>(asf, awin, G, k - 1 + APAD, rows, c);
-                                    packed_rows<RS>(asf, awin, G, k + APAD, rows, c);
+                                    // the window rows j-1, j, k-1, k from registers: row R holds (a_R, a_{R+1});
+                                    // a neighbour that is the other updated mode takes its new value
+                                    const float2 nj = P.nj, nk = P.nk;
+                                    const float2 jm = (j - 1 == k) ? nk : nb[0], jp = (j + 1 == k) ? nk : nb[1];
+                                    const float2 km = (k - 1 == j) ? nj : nb[2], kp = (k + 1 == j) ? nj : nb[3];
+                                    awin[(j - 1 + APAD) * G + c] = make_float4(jm.x, nj.x, jm.y, nj.y);
+                                    awin[(j + APAD) * G + c] = make_float4(nj.x, jp.x, nj.y, jp.y);
+                                    awin[(k - 1 + APAD) * G + c] = make_float4(km.x, nk.x, km.y, nk.y);
+                                    awin[(k + APAD) * G + c] = make_float4(nk.x, kp.x, nk.y, kp.y);
                                 }
                             }
                             if (warp == 0 && c < gr.count) {
@@ -859,7 +892,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                         }
                     }
                     red_par ^= 1;
-                    __syncwarp();
+                    if constexpr (kOneDecider) named_bar(1, NCT);
+                    else __syncwarp();
                 }
                 // interior measurement point: snapshot amplitudes and energies
                 const long long done = sweep_base + sw + 1;
