@@ -663,7 +663,7 @@ def profile_case():
 
 def profile_small():
     """Small cases for ncu, a few launches each: the batched N=64 workload itself (64 samples x 32 T x 2
-    replicas on the FP32 default 32 x 7 blocks: three 1-sweep launches; 26 MB of couplings, held by the L2 as
+    replicas on the FP32 default 32 x 11 blocks: three 1-sweep launches; 26 MB of couplings, held by the L2 as
     in the timed runs), then on N=256 (8 samples x 48 T x 2 replicas, 199 MB of couplings) one swap interval
     of 16 sweeps with its resync (energy_kernel), measurement (measure_kernel) and swap pass (swap_kernel),
     and the plain FP64 sweep (plain_sweep_kernel, the paper's design) for one sweep on 2 samples of N=64."""
@@ -674,7 +674,7 @@ def profile_small():
     Wb = workload.workloads()["n64_batched"]
     nq64 = len(pkg.enumerate_quads(64))
     Js = [workload.couplings(64, nq64, s) for s in Wb.seeds]
-    pt = pkg.PT(Wb.Ns, Js, Wb.temps, 2, 5, precision="fp32", chains_per_block=32, consumer_warps=7,
+    pt = pkg.PT(Wb.Ns, Js, Wb.temps, 2, 5, precision="fp32", chains_per_block=32, consumer_warps=11,
                 swap_every=0, measure_every=0, resync_every=0, use_graphs=False)
     for _ in range(3):
         pt.sweep(1)
@@ -763,7 +763,7 @@ def main(argv=None):
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     ap.add_argument("--profile-small", action="store_true",
-                    help="small cases for ncu: N=64 on 32 x 7 blocks, the N=256 resync/measure/swap kernels, the "
+                    help="small cases for ncu: N=64 on 32 x 11 blocks, the N=256 resync/measure/swap kernels, the "
                          "plain FP64 sweep")
     ap.add_argument("--profile-global", action="store_true",
                     help="run eight learned global-move rounds (for the launch list of a round) and exit")
