@@ -18,8 +18,9 @@ parallel Delta E, cross term of reading R5):
 Shapes: the N = 256 bench launch (16 samples x 48 T x 2 replicas, 8 chains x 11 field warps, packed FP32
 blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 96 on its 16-chain
 default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
-out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, ragged batches with the default and the autotuned shape
-(mixing the gathered and picked-out variants in one launch), and the FP64 kernels.  Updates include the first
+out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, N = 4 (one quadruplet) and N = 6, ragged batches with the
+default and the autotuned shape (mixing the gathered and picked-out variants in one launch), and the FP64
+kernels.  Updates include the first
 and last of a sweep and pairs at the ends of the mode range, adjacent pairs and j + k = N - 1.
 """
 import numpy as np
@@ -213,6 +214,8 @@ CASES = [
     ("n64_16x11", [64, 64], 2, 8, "fp32", 16, 11),
     ("n48_8chains_packed", [48, 48, 48], 2, 5, "fp32", 8, 0),
     ("n16_16x7", [16, 16], 2, 8, "fp32", 0, 0),
+    ("n4_single_quadruplet", [4, 4, 4], 2, 3, "fp32", 0, 0),
+    ("n6_fp64", [6, 6], 2, 3, "fp64", 0, 0),
     ("n24_8x7_packed", [24, 24], 2, 4, "fp32", 0, 0),
     ("ragged_mixed", [128, 32, 96, 48, 64, 96, 32], 2, 6, "fp32", 0, 0),
     ("n64_fp64_16x3", [64, 64], 2, 5, "fp64", 0, 0),
