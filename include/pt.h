@@ -197,8 +197,10 @@ int pt_fields(pt_ctx *ctx, int sample, int j, int k, double *out);
  * own proposal instead of B_jk and A_jk: there fields 6..9 hold Re sum_{q holding j and k} J_q (product of
  * the other two factors) dx_j dx_k (dx = conj(d) at positions 0 and 3, d at 1 and 2; the energy change is
  * then -cc Re[conj(dj) h_j + conj(dk) h_k] - cc * field 6) and three zeros.
- * Caller-owned host buffers; the call synchronises the context's stream.  PT_EINVAL for an update outside
- * [0, max N/2); PT_EUNSUPPORTED for PT_PREC_FP64_PLAIN. */
+ * Caller-owned host buffers; the call synchronises the context's stream.  The first call allocates the device
+ * buffer of the trace (n_chains * PT_TRACE_REC + 2 * (state size) doubles) and re-captures the sweep graphs.
+ * PT_EINVAL for an update outside [0, max N/2); PT_ENOMEM if that buffer cannot be allocated;
+ * PT_EUNSUPPORTED for PT_PREC_FP64_PLAIN. */
 #define PT_TRACE_REC 20
 int pt_trace_update(pt_ctx *ctx, int update, double *rec, double *a);
 

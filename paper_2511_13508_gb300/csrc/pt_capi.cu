@@ -199,7 +199,7 @@ struct pt_ctx {
     unsigned long long *d_mc_acc = nullptr, *d_mc_att = nullptr, *d_mcT_acc = nullptr, *d_mcT_att = nullptr;
     unsigned long long *d_swap_acc = nullptr, *d_swap_att = nullptr, *d_qhist = nullptr;
     double *d_stat = nullptr, *d_qstat = nullptr, *d_fields = nullptr;
-    double *d_trace = nullptr;  // update trace of the sweep kernel (blocked-store paths)
+    double *d_trace = nullptr;  // update trace of the sweep kernels (allocated by the first pt_trace_update)
     Control *d_ctl = nullptr;
     void *d_snap_a = nullptr;
     double *d_snap_E = nullptr;
@@ -1032,7 +1032,6 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
     RC(dalloc(c, &c->d_stat, (size_t)S * n_T * PT_NSTAT));
     RC(dalloc(c, &c->d_qstat, (size_t)S * n_T * PT_NQSTAT));
     RC(dalloc(c, &c->d_fields, (size_t)chains_ps * 8));
-    if (!c->plain) RC(dalloc(c, &c->d_trace, (size_t)c->n_chains * kTraceRec + (size_t)c->a_total * 2));
     RC(dalloc(c, &c->d_ctl, 1));
 
     // ---- couplings: blocked store (J-sharing paths) or canonical list + incidences (plain path)
@@ -1365,11 +1364,16 @@ int pt_fields(pt_ctx *c, int sample, int j, int k, double *out) {
 
 int pt_trace_update(pt_ctx *c, int update, double *rec, double *a) {
     if (!c || !rec) return fail(c, PT_EINVAL, "pt_trace_update: NULL argument");
-    if (!c->d_trace) return fail(c, PT_EUNSUPPORTED, "pt_trace_update: not available for PT_PREC_FP64_PLAIN");
+    if (c->plain) return fail(c, PT_EUNSUPPORTED, "pt_trace_update: not available for PT_PREC_FP64_PLAIN");
     if (update < 0 || update >= c->maxN / 2) return fail(c, PT_EINVAL, "pt_trace_update: update must be in [0, maxN/2)");
     int rc = watchdog_sync(c);
     if (rc != PT_OK) return rc;
     const size_t nrec = (size_t)c->n_chains * kTraceRec, bytes = (nrec + (size_t)c->a_total * 2) * sizeof(double);
+    if (!c->d_trace) {
+        // allocated on first use; the sweep graphs captured before hold no trace buffer and are rebuilt
+        if ((rc = dalloc(c, &c->d_trace, bytes / sizeof(double))) != PT_OK) return rc;
+        drop_graphs(c);
+    }
     CK(cudaMemsetAsync(c->d_trace, 0, bytes, c->stream));
     // arm the trace for the next sweep (its absolute index + 1), run it with its schedule, disarm
     struct { long long at; int u, pad; } on{c->sweeps_done + 1, update, 0}, off{0, -1, 0};
