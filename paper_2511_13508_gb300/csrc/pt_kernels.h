@@ -36,6 +36,7 @@ struct SweepParams {
     // update trace (armed by Control::trace_at / trace_update): [n_chains][kTraceRec] records, then the
     // pre-update states [a_total] as double complex, both in canonical (sample, replica, temperature) order
     double *trace;
+    int nst;                    // coupling ring stages (set by the launcher)
 };
 
 struct FieldsParams {

@@ -496,8 +496,12 @@ __device__ __forceinline__ bool metropolis_accept(double dH, double beta, double
 // The persistent sweep kernel.  NCW consumer warps + 1 producer warp.  A consumer lane is
 // (chain c = lane % G, worker q = lane / G); worker w = warp * (32/G) + q takes block w of every
 // chunk of CB = NCW*32/G blocks.  The producer warp streams the J runs of j and k, chunk by chunk,
-// into an NST-stage ring.  Work units = (group, run of sweeps) come from a ticket counter; a unit
+// into a ring of NST stages.  Work units = (group, run of sweeps) come from a ticket counter; a unit
 // waits (bounded) until the previous run of its group has been written back.
+// Ring depth: as many stages as fit next to the amplitude and window tables of the largest N (up to kNstMax), so
+// that the copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs).
+constexpr int kNstMax = 6, kNstMin = 2;
+
 template <typename real, int G, int NCW> struct SweepShape {
     static constexpr int WPW = 32 / G;
     static constexpr int NW = NCW * WPW;
@@ -506,22 +510,16 @@ template <typename real, int G, int NCW> struct SweepShape {
     static constexpr int NTHREADS = (NCW + 1) * 32;
     static constexpr int JS = JStride<real>::value;
     static constexpr size_t stage_bytes = (size_t)2 * CB * JS * sizeof(real);
-    // ring depth: as many stages (3..6) as fit next to an N = 256 amplitude table in ~210 KB, so that the
-    // copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs)
     static constexpr bool PACKED = sizeof(real) == 4;  // packed-FP32 block arithmetic (every FP32 shape)
-    static constexpr size_t amp_bytes_256 = (size_t)(256 + 2 * APAD) * RS * 2 * sizeof(real) +
-                                            (PACKED ? (size_t)(256 + 2 * APAD) * G * sizeof(float4) : 0);
-    static constexpr int NST_FIT = (int)((210 * 1024 - amp_bytes_256 - 8 * 1024) / stage_bytes);
-    static constexpr int NST = NST_FIT < 3 ? 3 : (NST_FIT > 6 ? 6 : NST_FIT);
 };
 
-template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
+// Shared memory of the sweep kernel without the coupling ring.
+template <typename real, int G, int NCW> size_t sweep_fixed_bytes(int maxN) {
     using Sh = SweepShape<real, G, NCW>;
     using V = typename vec2<real>::type;
     size_t b = 0;
-    b += 2 * Sh::NST * sizeof(uint64_t);                                  // mbarriers
+    b += 2 * kNstMax * sizeof(uint64_t);                                  // mbarriers
     b = (b + 127) / 128 * 128;
-    b += Sh::NST * Sh::stage_bytes;                                       // J ring
     b += (size_t)(maxN + 2 * APAD) * Sh::RS * sizeof(V);                  // amplitudes
     if (Sh::PACKED) b += (size_t)(maxN + 2 * APAD) * G * sizeof(float4);      // window table
     b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
@@ -533,19 +531,32 @@ template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN) {
     return b;
 }
 
+// Ring stages for the largest N within `limit` bytes of shared memory per block (0 when fewer than kNstMin fit).
+template <typename real, int G, int NCW> int sweep_stages(int maxN, size_t limit) {
+    const size_t fixed = sweep_fixed_bytes<real, G, NCW>(maxN), st = SweepShape<real, G, NCW>::stage_bytes;
+    if (fixed + kNstMin * st > limit) return 0;
+    const size_t n = (limit - fixed) / st;
+    return n > (size_t)kNstMax ? kNstMax : (int)n;
+}
+
+template <typename real, int G, int NCW> size_t sweep_smem_bytes(int maxN, int nst) {
+    return sweep_fixed_bytes<real, G, NCW>(maxN) + (size_t)nst * SweepShape<real, G, NCW>::stage_bytes;
+}
+
 template <typename real, int G, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams prm) {
     using Sh = SweepShape<real, G, NCW>;
     using V = typename vec2<real>::type;
-    constexpr int RS = Sh::RS, NST = Sh::NST, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS, NW = Sh::NW;
+    constexpr int RS = Sh::RS, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS, NW = Sh::NW;
+    const int NST = prm.nst;  // ring stages (kNstMin .. kNstMax), chosen by the launcher for the largest N
     constexpr int BT = (256 + NW - 1) / NW < 8 ? (256 + NW - 1) / NW : 8;  // B couplings held per lane
     constexpr int NCT = NCW * 32;  // consumer threads
     constexpr bool kOneDecider = G >= 16;  // one warp reduces and decides (see the update's decision step)
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + NST;
-    size_t off = (2 * NST * sizeof(uint64_t) + 127) / 128 * 128;
+    uint64_t *empty = full + kNstMax;
+    size_t off = (2 * kNstMax * sizeof(uint64_t) + 127) / 128 * 128;
     real *ring = reinterpret_cast<real *>(smem + off);
     off += NST * Sh::stage_bytes;
     V *as = reinterpret_cast<V *>(smem + off);
@@ -603,6 +614,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     const real *J = reinterpret_cast<const real *>(prm.J);
     V *A = reinterpret_cast<V *>(prm.a);
     uint32_t q = 0;  // global chunk counter (ring position)
+    // ring stage of chunk q (q mod NST) and the parity of its pass through the ring, advanced with q (NST is a
+    // launch parameter: no division per chunk)
+    int rst = 0;
+    uint32_t rph = 0;
     int red_par = 0;
 
     for (;;) {
@@ -688,9 +703,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     int j, k;
                     pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
                     const Ranges Rg = update_ranges(sd, bo_g, prm.mode_blk + sd.mode_off, j, k);
-                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q) {
-                        const int stage = q % NST;
-                        const uint32_t ph = (q / NST) & 1u;
+                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q, rph ^= (++rst == NST) ? 1u : 0u, rst = (rst == NST) ? 0 : rst) {
+                        const int stage = rst;
+                        const uint32_t ph = rph;
                         if (lane == 0) {
                             const bool ok = mbar_wait_bounded(&empty[stage], ph ^ 1u, prm.ctl, 2, abort_flag);
                             const int ce = min(cb + CB, Rg.uhi);
@@ -755,9 +770,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                             bcp[m] = sb < sB1 ? b_coupling<real>(J, s_bo, s_xtlo, Rg, sb, k) : real(0);
                         }
                     }
-                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q) {
-                        const int stage = q % NST;
-                        const uint32_t ph = (q / NST) & 1u;
+                    for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q, rph ^= (++rst == NST) ? 1u : 0u, rst = (rst == NST) ? 0 : rst) {
+                        const int stage = rst;
+                        const uint32_t ph = rph;
                         mbar_wait_bounded(&full[stage], ph, prm.ctl, 3, abort_flag);
                         const int b = cb + worker;
                         if (b < Rg.uhi && !*abort_flag) {
@@ -1109,18 +1124,33 @@ __global__ void energy_kernel(EnergyParams prm) {
 
 // ------------------------------------------------------------------------------------------------
 // host launchers
+// Opt-in shared memory per block of the current device.
+static size_t smem_limit() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return (size_t)v;
+}
+
 template <typename real, int G, int NCW>
 static cudaError_t launch_sweep_t(const SweepParams &p, int grid, cudaStream_t s) {
-    const size_t sm = sweep_smem_bytes<real, G, NCW>(p.maxN);
+    SweepParams q = p;
+    q.nst = sweep_stages<real, G, NCW>(p.maxN, smem_limit());
+    if (q.nst < kNstMin) return cudaErrorInvalidConfiguration;
+    const size_t sm = sweep_smem_bytes<real, G, NCW>(p.maxN, q.nst);
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<real, G, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    sweep_kernel<real, G, NCW><<<grid, (NCW + 1) * 32, sm, s>>>(p);
+    sweep_kernel<real, G, NCW><<<grid, (NCW + 1) * 32, sm, s>>>(q);
     return cudaGetLastError();
 }
 
 template <typename real, int G, int NCW>
 static int occupancy_t(int maxN) {
-    const size_t sm = sweep_smem_bytes<real, G, NCW>(maxN);
+    const int nst = sweep_stages<real, G, NCW>(maxN, smem_limit());
+    if (nst < kNstMin) return 0;
+    const size_t sm = sweep_smem_bytes<real, G, NCW>(maxN, nst);
     if (cudaFuncSetAttribute(sweep_kernel<real, G, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
     int nb = 0;

@@ -18,7 +18,8 @@ parallel Delta E, cross term of reading R5):
 Shapes: the N = 256 bench launch (16 samples x 48 T x 2 replicas, 8 chains x 11 field warps, packed FP32
 blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 96 on its 16-chain
 default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
-out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, N = 4 (one quadruplet) and N = 6, ragged batches with the
+out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, N = 4 (one quadruplet), N = 6 and the largest N = 512
+(FP32 and FP64: the coupling ring then holds fewer stages), ragged batches with the
 default and the autotuned shape (mixing the gathered and picked-out variants in one launch), and the FP64
 kernels.  Updates include the first
 and last of a sweep and pairs at the ends of the mode range, adjacent pairs and j + k = N - 1.
@@ -221,6 +222,8 @@ CASES = [
     ("n64_fp64_16x3", [64, 64], 2, 5, "fp64", 0, 0),
     ("n128_fp64_8x7", [128], 2, 4, "fp64", 0, 0),
     ("ragged_fp64", [40, 24, 64], 2, 3, "fp64", 0, 0),
+    ("n512_largest_fp32", [512], 2, 2, "fp32", 0, 0),
+    ("n512_largest_fp64", [512], 1, 2, "fp64", 0, 0),
 ]
 
 
