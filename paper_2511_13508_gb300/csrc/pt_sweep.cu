@@ -773,9 +773,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q, rph ^= (++rst == NST) ? 1u : 0u, rst = (rst == NST) ? 0 : rst) {
                         const int stage = rst;
                         const uint32_t ph = rph;
-                        mbar_wait_bounded(&full[stage], ph, prm.ctl, 3, abort_flag);
+                        // a chunk whose copies have landed is processed (its data are valid even after another
+                        // wait gave up); a wait that gives up, or sees the abort flag, skips it
+                        const bool landed = mbar_wait_bounded(&full[stage], ph, prm.ctl, 3, abort_flag);
                         const int b = cb + worker;
-                        if (b < Rg.uhi && !*abort_flag) {
+                        if (b < Rg.uhi && landed) {
                             const uint32_t info = __ldg(binfo + b);
                             const int st = (int)(info >> 16), xt = (int)(info & 0xffffu);
                             const int mode = ((b >= Rg.jlo && b < Rg.jhi) ? 1 : 0) | ((b >= Rg.klo && b < Rg.khi) ? 2 : 0);
