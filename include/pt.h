@@ -69,7 +69,9 @@ typedef struct pt_config {
     int chains_per_block; /* chains sharing one J stream inside a thread block: 0 = tuned, or 8/16/32 */
     int sweeps_per_unit;  /* sweeps in one scheduling unit of the persistent kernel; 0 = tuned */
     int blocks_per_sm;    /* persistent thread blocks per SM; 0 = tuned */
-    int consumer_warps;   /* field-computing warps per thread block (plus one copy warp); 0 = tuned */
+    int consumer_warps;   /* field-computing warps per thread block (plus one copy warp); 0 = tuned.  FP32:
+                           * 7, 11 or 15 with 8 or 16 chains per block, 3, 7, 9 or 11 with 32; FP64: 7 with 8
+                           * chains, 3 with 16 (PT_EINVAL otherwise) */
     int use_graphs;       /* replay each sweep segment as a captured CUDA graph (default 1) */
     int watchdog_ms;      /* host watchdog on synchronising calls; 0 = wait forever (default 600000) */
 } pt_config;

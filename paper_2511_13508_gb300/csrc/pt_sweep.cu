@@ -551,7 +551,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     const int NST = prm.nst;  // ring stages (kNstMin .. kNstMax), chosen by the launcher for the largest N
     constexpr int BT = (256 + NW - 1) / NW < 8 ? (256 + NW - 1) / NW : 8;  // B couplings held per lane
     constexpr int NCT = NCW * 32;  // consumer threads
-    constexpr bool kOneDecider = G >= 16;  // one warp reduces and decides (see the update's decision step)
+    // decision step (see the end of an update): 16 chains per block spread it over 8 lanes per chain, 32 chains
+    // leave it to warp 0, 8 chains take it redundantly in every warp
+    constexpr bool kSpread = G == 16;
+    constexpr bool kOneDecider = G == 32;
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -821,7 +824,21 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
 #pragma unroll
                         for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
                     real *rb = red + (size_t)red_par * NCW * G * 8;
-                    if constexpr (Sh::PACKED) {
+                    if constexpr (kSpread) {
+                        // layout [warp][chain][value]: the 8 values of one (warp, chain) are consecutive, so that the
+                        // reads after the barrier (32 lanes = 4 chains x 8 values of one warp) are 32 consecutive words
+                        if (wq == 0) {
+                            if constexpr (sizeof(real) == 4) {
+                                float4 *d = reinterpret_cast<float4 *>(rb + ((size_t)warp * G + c) * 8);
+                                d[0] = make_float4(v[0], v[1], v[2], v[3]);
+                                d[1] = make_float4(v[4], v[5], v[6], v[7]);
+                            } else {
+                                double2 *d = reinterpret_cast<double2 *>(rb + ((size_t)warp * G + c) * 8);
+                                d[0] = make_double2(v[0], v[1]); d[1] = make_double2(v[2], v[3]);
+                                d[2] = make_double2(v[4], v[5]); d[3] = make_double2(v[6], v[7]);
+                            }
+                        }
+                    } else if constexpr (Sh::PACKED) {
                         // layout [half][warp][chain] of float4: the chains of one (half, warp) are consecutive, so
                         // the stores and the reads after the barrier are free of bank conflicts
                         float4 *rb4 = reinterpret_cast<float4 *>(rb);
@@ -841,19 +858,74 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     // packed: the neighbours of j and k for the window rows rewritten on acceptance (modes other
                     // than j and k keep their values during this update)
                     float2 nb[4];
-                    if (Sh::PACKED && (!kOneDecider || warp == 0)) {
+                    if (Sh::PACKED && !kSpread && (!kOneDecider || warp == 0)) {
                         const float2 *asf = reinterpret_cast<const float2 *>(as);
                         nb[0] = asf[(j - 1 + APAD) * RS + c]; nb[1] = asf[(j + 1 + APAD) * RS + c];
                         nb[2] = asf[(k - 1 + APAD) * RS + c]; nb[3] = asf[(k + 1 + APAD) * RS + c];
                     }
                     named_bar(1, NCT);
-                    // 16 and 32 chains per block: warp 0 alone forms the totals, takes the decision and writes the
-                    // new amplitudes, windows, energies and counters, and a second barrier orders those writes
-                    // before every warp's next update (every other warp would repeat the same reads of all
-                    // partial sums: NCW x G x 8 words each).  8 chains per block: every warp forms the same totals
-                    // in the same order, takes the same decision and writes the same values, with no second
-                    // barrier (measured faster at N = 256).
-                    if (!kOneDecider || warp == 0) {
+                    // Decision (measured on GB300, per shape):
+                    // - 16 chains per block: 8 lanes per chain, 4 chains per warp, warps in turn.  Lane e of a
+                    //   chain's group adds value e over the warps in warp order; the group's first lane gathers
+                    //   the 8 totals, decides and writes (+3.7% over warp 0 alone at N = 64);
+                    // - 32 chains per block: warp 0 alone forms the totals, decides and writes (every other warp
+                    //   would repeat the same reads of all partial sums: NCW x G x 8 words each; the 8-lane
+                    //   groups measured 1.5% slower here);
+                    // - 8 chains per block: every warp forms the same totals in the same order, takes the same
+                    //   decision and writes the same values, with no second barrier (measured faster at N = 256).
+                    // With one or more deciding warps a second barrier orders their writes before every warp's next
+                    // update.
+                    if constexpr (kSpread) {
+                        for (int c4 = warp * 4; c4 < G; c4 += NCW * 4) {  // warp-uniform trip count
+                            const int cd = c4 + (lane >> 3), e = lane & 7;
+                            const bool mine = cd < G, lead = mine && e == 0;
+                            // packed: the neighbours of j and k for the window rows rewritten on acceptance (modes
+                            // other than j and k keep their values during this update)
+                            float2 nbs[4];
+                            if (Sh::PACKED && lead) {
+                                const float2 *asf = reinterpret_cast<const float2 *>(as);
+                                nbs[0] = asf[(j - 1 + APAD) * RS + cd]; nbs[1] = asf[(j + 1 + APAD) * RS + cd];
+                                nbs[2] = asf[(k - 1 + APAD) * RS + cd]; nbs[3] = asf[(k + 1 + APAD) * RS + cd];
+                            }
+                            real s = 0;
+                            if (mine) {
+#pragma unroll
+                                for (int w = 0; w < NCW; ++w) s += rb[((size_t)w * G + cd) * 8 + e];
+                            }
+                            real t[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) t[i] = __shfl_sync(0xffffffffu, s, (lane & ~7) | i);
+                            if (lead) {
+                                Partials<real> f;
+                                f.hj.x = t[0]; f.hj.y = t[1]; f.hk.x = t[2]; f.hk.y = t[3];
+                                f.B.x = t[4]; f.B.y = t[5]; f.A.x = t[6]; f.A.y = t[7];
+                                const Proposal<real> P = Pp[cd];
+                                const real dH = delta_h<real>(P, f, cc);
+                                const bool live = cd < gr.count;
+                                const bool acc = live && metropolis_accept(dH, cBeta[cd], P.U);
+                                if (tr_at == sweep_base + sw + 1 && u == tr_u && live)
+                                    trace_write<real, RS>(prm.trace, prm.n_chains, sd.a_off, sd.chain0, N, cId[cd], j, k, f, P,
+                                                          dH, acc, cBeta[cd], cE[cd], as, cd);
+                                if (acc) {
+                                    as[(j + APAD) * RS + cd] = P.nj;
+                                    as[(k + APAD) * RS + cd] = P.nk;
+                                    if constexpr (Sh::PACKED) {
+                                        const float2 nj = P.nj, nk = P.nk;
+                                        const float2 jm = (j - 1 == k) ? nk : nbs[0], jp = (j + 1 == k) ? nk : nbs[1];
+                                        const float2 km = (k - 1 == j) ? nj : nbs[2], kp = (k + 1 == j) ? nj : nbs[3];
+                                        awin[(j - 1 + APAD) * G + cd] = make_float4(jm.x, nj.x, jm.y, nj.y);
+                                        awin[(j + APAD) * G + cd] = make_float4(nj.x, jp.x, nj.y, jp.y);
+                                        awin[(k - 1 + APAD) * G + cd] = make_float4(km.x, nk.x, km.y, nk.y);
+                                        awin[(k + APAD) * G + cd] = make_float4(nk.x, kp.x, nk.y, kp.y);
+                                    }
+                                }
+                                if (live) {
+                                    if (acc) { cE[cd] += (double)dH; cAcc[cd] += 1u; }
+                                    cAtt[cd] += 1ull;
+                                }
+                            }
+                        }
+                    } else if (!kOneDecider || warp == 0) {
                         // lane (c, wq) adds the partials of warps wq, wq + WPW, ...: the trip count is the
                         // same on every lane (predicated body), so the warp is converged at the shuffles
                         real t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -909,7 +981,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                         }
                     }
                     red_par ^= 1;
-                    if constexpr (kOneDecider) named_bar(1, NCT);
+                    if constexpr (kOneDecider || kSpread) named_bar(1, NCT);
                     else __syncwarp();
                 }
                 // interior measurement point: snapshot amplitudes and energies
@@ -1161,12 +1233,10 @@ static int occupancy_t(int maxN) {
     return nb;
 }
 
-#define PT_SWEEP_VARIANTS(X)                        \
-    X(float, 8, 7) X(float, 8, 11) X(float, 8, 15)  \
-    X(float, 8, 12) X(float, 8, 13) X(float, 8, 14) \
-    X(float, 16, 14) X(float, 32, 14) X(float, 16, 15) \
-    X(float, 16, 7) X(float, 16, 11)                \
-    X(float, 32, 3) X(float, 32, 7) X(float, 32, 9) X(float, 32, 11) \
+#define PT_SWEEP_VARIANTS(X)                                          \
+    X(float, 8, 7) X(float, 8, 11) X(float, 8, 15)                    \
+    X(float, 16, 7) X(float, 16, 11) X(float, 16, 15)                 \
+    X(float, 32, 3) X(float, 32, 7) X(float, 32, 9) X(float, 32, 11)  \
     X(double, 8, 7) X(double, 16, 3)
 
 bool sweep_variant_exists(bool dbl, int G, int ncw) {
