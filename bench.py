@@ -664,7 +664,8 @@ def profile_case():
 def profile_small():
     """Small cases for ncu, a few launches each: the batched N=64 workload itself (64 samples x 32 T x 2
     replicas on the FP32 default 32 x 11 blocks: three 1-sweep launches; 26 MB of couplings, held by the L2 as
-    in the timed runs), then on N=256 (8 samples x 48 T x 2 replicas, 199 MB of couplings) one swap interval
+    in the timed runs), the ragged batch (96 samples, N in {32 .. 128}, 24 T x 2 replicas, default 16 x 11
+    blocks: three 1-sweep launches), then on N=256 (8 samples x 48 T x 2 replicas, 199 MB of couplings) one swap interval
     of 16 sweeps with its resync (energy_kernel), measurement (measure_kernel) and swap pass (swap_kernel),
     and the plain FP64 sweep (plain_sweep_kernel, the paper's design) for one sweep on 2 samples of N=64."""
     import torch
@@ -676,6 +677,14 @@ def profile_small():
     Js = [workload.couplings(64, nq64, s) for s in Wb.seeds]
     pt = pkg.PT(Wb.Ns, Js, Wb.temps, 2, 5, precision="fp32", chains_per_block=32, consumer_warps=11,
                 swap_every=0, measure_every=0, resync_every=0, use_graphs=False)
+    for _ in range(3):
+        pt.sweep(1)
+    pt.sync()
+    pt.close()
+    Wr = workload.workloads()["ragged"]
+    Js = [workload.couplings(n, len(pkg.enumerate_quads(n)), s) for n, s in zip(Wr.Ns, Wr.seeds)]
+    pt = pkg.PT(Wr.Ns, Js, Wr.temps, Wr.replicas, 5, precision="fp32", swap_every=0, measure_every=0,
+                resync_every=0, use_graphs=False)
     for _ in range(3):
         pt.sweep(1)
     pt.sync()
@@ -763,8 +772,8 @@ def main(argv=None):
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: N=256, 8 samples x 48 T x 2 replicas, three 1-sweep launches")
     ap.add_argument("--profile-small", action="store_true",
-                    help="small cases for ncu: N=64 on 32 x 11 blocks, the N=256 resync/measure/swap kernels, the "
-                         "plain FP64 sweep")
+                    help="small cases for ncu: N=64 on 32 x 11 blocks, the ragged batch on 16 x 11, the N=256 "
+                         "resync/measure/swap kernels, the plain FP64 sweep")
     ap.add_argument("--profile-global", action="store_true",
                     help="run eight learned global-move rounds (for the launch list of a round) and exit")
     ap.add_argument("--profile-graph", action="store_true",

@@ -928,24 +928,31 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
 
     // ---- scheduling shape
     const int chains_ps = replicas * n_T;
-    // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300:
-    // N >= 128: 8 chains x 11 warps; 48 <= N < 128: the most chains per block (32, 16, 8) that still give
-    // about one group per SM (N = 64: 32 x 11 for 64 samples x 64 chains, 22.3M chain-sweeps/s, against
-    // 11.9M with 8 x 11; but 8 x 11 for 16 samples x 64 chains, 10.0M against 5.7M with 32 x 11, which
-    // leaves most SMs idle), 32 x 11 when none does; N < 48: 16 x 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3
+    // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300 (chain-sweeps/s):
+    // - N >= 160: 8 chains x 11 warps (N = 192, 32 samples x 64 chains: 1.48M against 1.41M with 16 x 11; N = 256,
+    //   16 x 96 chains: 0.694M against 0.481M);
+    // - 48 <= N < 160: the most chains per block that still give about one group per SM, from 32, 16, 8 below
+    //   N = 96 and from 16, 8 above (N = 64, 64 samples x 64 chains: 32 x 11 24.2M against 20.8M with 16 x 11
+    //   and 12.5M with 8 x 11; 16 samples x 64 chains: 8 x 11 10.0M against 5.7M with 32 x 11, which leaves most
+    //   SMs idle; N = 128, 64 samples x 64 chains: 16 x 11 4.71M against 4.50M with 32 x 11 and 3.81M with
+    //   8 x 11; the ragged batch N in {32..128}: 16 x 11 8.91M against 8.38M with 8 x 11), 32 x 11 (16 x 11 from
+    //   N = 96) when none does;
+    // - N < 48: 16 x 7.
+    // FP64: 8 x 7 from N = 128 on, else 16 x 3
     int G = cfg.chains_per_block, ncw = 0;
     if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
     if (G == 0) {
         if (c->dbl) G = (c->maxN >= 128) ? 8 : 16;  // FP64, N = 64, 64 samples: 16 x 3 685k, 8 x 7 521k
-        else if (c->maxN >= 128) G = 8;
+        else if (c->maxN >= 160) G = 8;
         else if (c->maxN >= 48) {
             int dev = 0, sms = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 0;
+            const int gmax = c->maxN >= 96 ? 16 : 32;
             for (int g : {32, 16, 8}) {
-                if (G == 0 && sms > 0 && (int64_t)S * ((chains_ps + g - 1) / g) >= (int64_t)sms * 4 / 5) G = g;
+                if (G == 0 && g <= gmax && sms > 0 && (int64_t)S * ((chains_ps + g - 1) / g) >= (int64_t)sms * 4 / 5) G = g;
             }
-            if (G == 0) G = chains_ps >= 32 ? 32 : 16;
+            if (G == 0) G = (gmax == 32 && chains_ps >= 32) ? 32 : 16;
         } else {
             G = 16;
         }

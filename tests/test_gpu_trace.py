@@ -16,8 +16,8 @@ parallel Delta E, cross term of reading R5):
   - beta and, for FP64, the running energy against H(state).
 
 Shapes: the N = 256 bench launch (16 samples x 48 T x 2 replicas, 8 chains x 11 field warps, packed FP32
-blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 96 on its 16-chain
-default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
+blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 128 and 96 on their
+16-chain default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
 out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, N = 4 (one quadruplet), N = 6 and the largest N = 512
 (FP32 and FP64: the coupling ring then holds fewer stages), ragged batches with the
 default and the autotuned shape (mixing the gathered and picked-out variants in one launch), and the FP64
@@ -207,7 +207,8 @@ def run_traces(pt, Ns, Js, temps, R, nT, seed, prec, n_calls, chains_per_sample=
 
 CASES = [
     # name, Ns, R, nT, precision, chains_per_block, consumer_warps
-    ("n128_8x11_gatherB", [128, 128], 2, 6, "fp32", 0, 0),
+    ("n128_8x11_gatherB", [128, 128], 2, 6, "fp32", 8, 11),
+    ("n128_default_16chains", [128, 128], 2, 8, "fp32", 0, 0),
     ("n96_8x11_gatherB", [96, 96], 2, 5, "fp32", 8, 11),
     ("n96_default_16chains", [96, 96], 2, 8, "fp32", 0, 0),
     ("n64_32x7", [64, 64], 2, 16, "fp32", 32, 7),
