@@ -375,12 +375,12 @@ __device__ __forceinline__ Ranges update_ranges(const SampleDev &sd, const int *
     return R;
 }
 
-// Smallest N for which the sweep kernel gathers the B_jk couplings once per update (b_coupling) instead of
-// picking them out of the blocks (measured on GB300: faster from N = 128 on, slower at N = 16 and 64).
-constexpr int kGatherBMinN = 96;
-// ... compiled into the FP32 shapes of 8 chains per block only (the large-N shapes); the others keep no trace
-// of it (their per-update work is too small to hide any fixed cost)
-template <typename real, int G> constexpr bool kGatherB = sizeof(real) == 4 && G == 8;
+// Smallest N for which the FP32 sweep kernel gathers the B_jk couplings once per update (b_coupling, by the copy
+// warp into a shared buffer) instead of picking them out of the blocks.  Measured on GB300 (chain-sweeps/s): with
+// the gather from N = 48 on every FP32 shape, the ragged batch on 16 x 11 8.72M -> 8.82M and on 8 x 11 8.53M ->
+// 8.62M, the others unchanged; when the field warps still did the gather themselves it paid only from N = 128 on.
+constexpr int kGatherBMinN = 48;
+template <typename real, int G> constexpr bool kGatherB = sizeof(real) == 4;
 
 // The coupling J_j[s][{k, s-k}] of quadruplet {j, s-j, k, s-k} (0 where the store holds no such entry):
 // column x* = min(k, s-k) of row s in mode j's run, read from global memory (L2-resident: the run is
@@ -501,6 +501,9 @@ __device__ __forceinline__ bool metropolis_accept(double dH, double beta, double
 // Ring depth: as many stages as fit next to the amplitude and window tables of the largest N (up to kNstMax), so
 // that the copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs).
 constexpr int kNstMax = 6, kNstMin = 2;
+// Buffers of gathered B_jk couplings (large N, 8 chains per block): the copy warp fills the buffer of an update
+// while it streams the update's coupling runs, up to kBD updates ahead of the field warps.
+constexpr int kBD = 4;
 
 template <typename real, int G, int NCW> struct SweepShape {
     static constexpr int WPW = 32 / G;
@@ -518,10 +521,11 @@ template <typename real, int G, int NCW> size_t sweep_fixed_bytes(int maxN) {
     using Sh = SweepShape<real, G, NCW>;
     using V = typename vec2<real>::type;
     size_t b = 0;
-    b += 2 * kNstMax * sizeof(uint64_t);                                  // mbarriers
+    b += 2 * (kNstMax + kBD) * sizeof(uint64_t);                          // mbarriers
     b = (b + 127) / 128 * 128;
     b += (size_t)(maxN + 2 * APAD) * Sh::RS * sizeof(V);                  // amplitudes
     if (Sh::PACKED) b += (size_t)(maxN + 2 * APAD) * G * sizeof(float4);      // window table
+    if (kGatherB<real, G>) b += (size_t)kBD * maxN * sizeof(real);            // gathered B_jk couplings
     b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
     b += (size_t)2 * G * sizeof(Proposal<real>) + 16;                     // proposals, double-buffered
     b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
@@ -549,7 +553,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     using V = typename vec2<real>::type;
     constexpr int RS = Sh::RS, CB = Sh::CB, WPW = Sh::WPW, JS = Sh::JS, NW = Sh::NW;
     const int NST = prm.nst;  // ring stages (kNstMin .. kNstMax), chosen by the launcher for the largest N
-    constexpr int BT = (256 + NW - 1) / NW < 8 ? (256 + NW - 1) / NW : 8;  // B couplings held per lane
     constexpr int NCT = NCW * 32;  // consumer threads
     // decision step (see the end of an update): 16 chains per block spread it over 8 lanes per chain, 32 chains
     // leave it to warp 0, 8 chains take it redundantly in every warp
@@ -559,7 +562,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + kNstMax;
-    size_t off = (2 * kNstMax * sizeof(uint64_t) + 127) / 128 * 128;
+    uint64_t *bfull = empty + kNstMax;  // B-coupling buffers: filled (32 copy-warp lanes) / read (NCW warps)
+    uint64_t *bempty = bfull + kBD;
+    size_t off = (2 * (kNstMax + kBD) * sizeof(uint64_t) + 127) / 128 * 128;
     real *ring = reinterpret_cast<real *>(smem + off);
     off += NST * Sh::stage_bytes;
     V *as = reinterpret_cast<V *>(smem + off);
@@ -568,6 +573,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     if (Sh::PACKED) {
         awin = reinterpret_cast<float4 *>(smem + off);
         off += (size_t)(prm.maxN + 2 * APAD) * G * sizeof(float4);
+    }
+    real *bvals = nullptr;  // [kBD][maxN]: B_jk couplings of an update, s = max(j,k) + i
+    if (kGatherB<real, G>) {
+        bvals = reinterpret_cast<real *>(smem + off);
+        off += (size_t)kBD * prm.maxN * sizeof(real);
     }
     real *red = reinterpret_cast<real *>(smem + off);
     off += (size_t)2 * NCW * G * 8 * sizeof(real);
@@ -605,6 +615,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], NCW);
         }
+        for (int i = 0; i < kBD; ++i) {
+            mbar_init(&bfull[i], 32);
+            mbar_init(&bempty[i], NCW);
+        }
         s_unit[2] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -622,6 +636,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     int rst = 0;
     uint32_t rph = 0;
     int red_par = 0;
+    uint32_t bcnt = 0;  // updates with gathered B couplings so far (buffer bcnt % kBD, phase (bcnt / kBD) & 1)
 
     for (;;) {
         __syncthreads();
@@ -652,6 +667,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
         const SampleDev sd = prm.samples[gr.sample];
         const int N = sd.N;
         const int sw0 = ci * spu, sw1 = min(n_sweeps, sw0 + spu);
+        const bool gatherB = kGatherB<real, G> && N >= kGatherBMinN;
 
         // ---- unit set-up: tables, chain metadata, amplitudes (consumers); producer starts streaming
         if (!producer) {
@@ -697,6 +713,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
         if (producer) {
             // ---------------- producer warp: stream J runs of (j,k) for every update of the unit
             const int *bo_g = prm.bo + sd.tab_off;
+            const int *xtlo_g = prm.xtlo + sd.tab_off;
             bool stop = false;
             for (int sw = sw0; sw < sw1 && !stop; ++sw) {
                 const uint32_t sweep = (uint32_t)(sweep_base + sw);
@@ -706,6 +723,20 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     int j, k;
                     pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
                     const Ranges Rg = update_ranges(sd, bo_g, prm.mode_blk + sd.mode_off, j, k);
+                    if (kGatherB<real, G> && gatherB) {
+                        // the update's B_jk couplings J_j[s][{k, s-k}], s in [max(j,k), min(j,k) + N), gathered
+                        // from L2 by the 32 lanes into a buffer that the field warps read after their blocks
+                        const int slot = (int)(bcnt % kBD);
+                        const uint32_t bph = (bcnt / kBD) & 1u;
+                        ++bcnt;
+                        if (mbar_wait_bounded(&bempty[slot], bph ^ 1u, prm.ctl, 4, abort_flag)) {
+                            const int sB0 = max(j, k), nB = min(j, k) + N - sB0;
+                            real *bv = bvals + (size_t)slot * prm.maxN;
+                            for (int i = lane; i < nB; i += 32)
+                                bv[i] = b_coupling<real>(J, bo_g, xtlo_g, Rg, sB0 + i, k);
+                        }
+                        mbar_arrive(&bfull[slot]);
+                    }
                     for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q, rph ^= (++rst == NST) ? 1u : 0u, rst = (rst == NST) ? 0 : rst) {
                         const int stage = rst;
                         const uint32_t ph = rph;
@@ -733,7 +764,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             // update trace: absolute sweep + 1 and update to record (0 = none)
             const long long tr_at = prm.trace ? prm.ctl->trace_at : 0ll;
             const int tr_u = prm.trace ? prm.ctl->trace_update : -1;
-            const bool gatherB = kGatherB<real, G> && N >= kGatherBMinN;
             const real cc = (real)prm.cc;
             for (int sw = sw0; sw < sw1; ++sw) {
                 const uint32_t sweep = (uint32_t)(sweep_base + sw);
@@ -759,20 +789,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     pr.zero();
                     PartialsX2 prx;
                     prx.zero();
-                    // B_jk = sum_s conj(a_{s-j}) J_j[s][{k, s-k}] a_{s-k} over s in [max(j,k), min(j,k)+N): the
-                    // couplings are loaded here (one per worker and BT-slot, shared by its chains) and used after
-                    // the chunk loop, so their latency hides behind it
-                    // (large N only: for small N the per-update gather costs more than picking the elements out
-                    // of the blocks, which process_block then does)
-                    const int sB0 = max(j, k), sB1 = gatherB ? min(j, k) + N : sB0;
-                    real bcp[BT];
-                    if (kGatherB<real, G>) {
-#pragma unroll
-                        for (int m = 0; m < BT; ++m) {
-                            const int sb = sB0 + worker + m * NW;
-                            bcp[m] = sb < sB1 ? b_coupling<real>(J, s_bo, s_xtlo, Rg, sb, k) : real(0);
-                        }
-                    }
                     for (int cb = Rg.ulo; cb < Rg.uhi; cb += CB, ++q, rph ^= (++rst == NST) ? 1u : 0u, rst = (rst == NST) ? 0 : rst) {
                         const int stage = rst;
                         const uint32_t ph = rph;
@@ -807,15 +823,21 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                         pr.B.x = prx.B.x; pr.B.y = prx.B.y;
                         pr.A.x = prx.A.x; pr.A.y = prx.A.y;
                     }
-                    if (kGatherB<real, G>) {
-#pragma unroll
-                        for (int m = 0; m < BT; ++m) {
-                            const int sb = sB0 + worker + m * NW;
-                            if (sb < sB1) caxpy(pr.B, bcp[m], cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
+                    // B_jk = sum_s conj(a_{s-j}) J_j[s][{k, s-k}] a_{s-k} over s in [max(j,k), min(j,k)+N) (large N: the
+                    // couplings come from the buffer the copy warp filled; worker w takes s = max(j,k) + w + m NW;
+                    // for smaller N process_block picks them out of the blocks)
+                    if (kGatherB<real, G> && gatherB) {
+                        const int slot = (int)(bcnt % kBD);
+                        const uint32_t bph = (bcnt / kBD) & 1u;
+                        ++bcnt;
+                        if (mbar_wait_bounded(&bfull[slot], bph, prm.ctl, 5, abort_flag)) {
+                            const real *bv = bvals + (size_t)slot * prm.maxN;
+                            const int sB0 = max(j, k), sB1 = min(j, k) + N;
+                            for (int sb = sB0 + worker; sb < sB1; sb += NW)
+                                caxpy(pr.B, bv[sb - sB0], cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
                         }
-                        for (int sb = sB0 + worker + BT * NW; sb < sB1; sb += NW)  // N > BT * NW only
-                            caxpy(pr.B, b_coupling<real>(J, s_bo, s_xtlo, Rg, sb, k),
-                                  cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bempty[slot]);
                     }
                     // reduce over the workers of this warp, then across warps through shared memory
                     real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};

@@ -154,8 +154,8 @@ def oracle_n64_blocks():
 
 @pytest.mark.parametrize("cpb,cw", [(32, 11), (16, 11)])
 def test_fp32_long_run_matches_oracle_at_n64_production_shapes(cpb, cw, oracle_n64_blocks):
-    """N = 64 on the batched workload's block shapes (32 x 11, 16 x 11: packed FP32 blocks, B picked out of the
-    blocks): independent FP32 GPU and FP64 oracle runs on the same couplings; per (sample, T) block means of
+    """N = 64 on the batched workload's block shapes (32 x 11, 16 x 11: packed FP32 blocks, B_jk gathered by
+    the copy warp): independent FP32 GPU and FP64 oracle runs on the same couplings; per (sample, T) block means of
     E/N, C_V/N (Eq. (21)), <q^2> (Sec. IV.C), Y2 and Y4 (Sec. IV.D), and P(q) per T pooled over samples, agree
     within their block errors."""
     N, S, R, nT, burn, nb, sw = (N64[k] for k in ("N", "S", "R", "nT", "burn", "nb", "sw"))

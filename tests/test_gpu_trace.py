@@ -16,9 +16,9 @@ parallel Delta E, cross term of reading R5):
   - beta and, for FP64, the running energy against H(state).
 
 Shapes: the N = 256 bench launch (16 samples x 48 T x 2 replicas, 8 chains x 11 field warps, packed FP32
-blocks, B_jk gathered from L2), N = 128 and 96 on 8 x 11 (the gather threshold), N = 128 and 96 on their
-16-chain default (16 x 11), N = 64 on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (packed, B picked
-out of the blocks), N = 24 on 8 x 7, N = 16 on 16 x 7, N = 4 (one quadruplet), N = 6 and the largest N = 512
+blocks, B_jk gathered by the copy warp), N = 128 and 96 on 8 x 11 and on their 16-chain default (16 x 11), N = 64
+on 32 x 7, 32 x 11 (its default) and 16 x 11, N = 48 on 8 chains (the gather threshold), N = 32 on 32 x 7, N = 24
+on 8 x 7 and N = 16 on 16 x 7 (B picked out of the blocks), N = 4 (one quadruplet), N = 6 and the largest N = 512
 (FP32 and FP64: the coupling ring then holds fewer stages), ragged batches with the
 default and the autotuned shape (mixing the gathered and picked-out variants in one launch), and the FP64
 kernels.  Updates include the first
@@ -215,6 +215,7 @@ CASES = [
     ("n64_default_32x11", [64, 64], 2, 16, "fp32", 0, 0),
     ("n64_16x11", [64, 64], 2, 8, "fp32", 16, 11),
     ("n48_8chains_packed", [48, 48, 48], 2, 5, "fp32", 8, 0),
+    ("n32_32x7_picked_B", [32, 32], 2, 16, "fp32", 32, 7),
     ("n16_16x7", [16, 16], 2, 8, "fp32", 0, 0),
     ("n4_single_quadruplet", [4, 4, 4], 2, 3, "fp32", 0, 0),
     ("n6_fp64", [6, 6], 2, 3, "fp64", 0, 0),
