@@ -214,6 +214,8 @@ struct pt_ctx {
     std::vector<cudaGraph_t> graph_defs;
     bool own_stream = false;
     size_t max_groups = 0;  // capacity of d_groups / d_progress (groups of 8 chains)
+    int sms = 0;            // streaming multiprocessors of the device
+    double *d_epart = nullptr;  // partial energies of the resync, [max_groups][kEnergyPartsMax][32]
     LearnState *learn = nullptr;
     unsigned long long *d_gm_acc = nullptr, *d_gm_att = nullptr;  // [S][nT] global-move counters
 };
@@ -316,8 +318,14 @@ int run_energy(pt_ctx *c, int renorm, double *E_out, bool write_state) {
     p.samples = c->d_samples; p.groups = c->d_groups; p.J = c->d_J; p.bo = c->d_bo; p.blkinfo = c->d_blkinfo;
     p.mode_blk = c->d_mode_blk; p.ebo = c->d_ebo; p.a = c->d_a; p.cc = c->cfg.cc_factor; p.renorm = renorm;
     p.E_out = E_out; p.E_state = write_state ? c->d_E : nullptr; p.ctl = c->d_ctl;
+    // several thread blocks per group (their partial sums added in a fixed order by a second kernel), so that the
+    // resync fills the GPU with more warps than one block per group gives (about 8 blocks per SM; measured on
+    // GB300: see the energy kernel)
+    const int ng = (int)c->groups.size();
+    p.part = c->d_epart;
+    p.parts = std::max(1, std::min(kEnergyPartsMax, (8 * std::max(c->sms, 1) + ng - 1) / std::max(ng, 1)));
     const int Ge = c->dbl ? std::min(c->G, 16) : c->G;
-    CK(launch_energy(c->dbl, Ge, p, (int)c->groups.size(), c->maxN, c->stream));
+    CK(launch_energy(c->dbl, Ge, p, ng, c->maxN, c->stream));
     return PT_OK;
 }
 
@@ -1137,6 +1145,8 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
         if (occ < 1) return bail(fail(c, PT_EUNSUPPORTED, "pt_create: sweep kernel does not fit on this GPU for this N"));
         const int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
         c->grid = std::max(1, std::min((int)c->groups.size(), sms * bps));
+        c->sms = sms;
+        RC(dalloc(c, &c->d_epart, c->max_groups * (size_t)kEnergyPartsMax * 32));
     }
 
     // ---- initial chains (exact beta = 0 draws) and their energies

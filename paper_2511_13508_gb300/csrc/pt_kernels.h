@@ -66,7 +66,10 @@ struct EnergyParams {
     double *E_out;   // optional: energies by chain slot
     double *E_state; // optional: running-energy array to overwrite
     Control *ctl;
+    double *part;    // partial sums [group][part][32] (kEnergyPartsMax parts at most)
+    int parts;       // thread blocks per group (1 .. kEnergyPartsMax)
 };
+constexpr int kEnergyPartsMax = 8;
 
 // pt_sweep.cu
 bool sweep_variant_exists(bool dbl, int G, int ncw);

@@ -1112,20 +1112,52 @@ __global__ void fields_kernel(FieldsParams prm) {
 //     H = -cc sum_x Re( conj(a_x) h^>_x ),
 // which visits every quadruplet once, at its smallest mode x (partner m: the largest; the pair {p, q} of
 // the two middle modes has p > x).  Blocks whose columns all lie at or below x are skipped.  Products and
-// row sums in `real`, per-block sums accumulated in FP64.  With renorm != 0 the chain is first rescaled
-// onto sum |a|^4 = N.
+// row sums in `real`, per-block sums accumulated in FP64.  A group's blocks are split over prm.parts thread
+// blocks (block b of part p takes the work items p NW + worker, stepping by parts NW); each writes its per-chain
+// FP64 sums to prm.part and energy_sum_kernel adds the parts in order.  With renorm != 0, renorm_kernel first
+// rescales every chain onto sum |a|^4 = N.  The kernel waits on coupling loads from L2, so it runs as many
+// warps per SM as fit: 3 blocks of 256 threads (FP32; 2 for FP64) and about 8 blocks per SM in all.  Measured on
+// GB300 (resync of the N = 256 bench workload, 192 groups): 2.81 ms with one block per group, 2.08 ms with about
+// 4 blocks per SM at 2 per SM, 1.45 ms now; batched N = 64: 0.166 -> 0.12 ms, ragged batch: 0.58 -> 0.24 ms.
 template <typename real, int G>
-__global__ void energy_kernel(EnergyParams prm) {
+__global__ void __launch_bounds__(256) renorm_kernel(EnergyParams prm) {
+    using V = typename vec2<real>::type;
+    const GroupDev gr = prm.groups[blockIdx.x];
+    const SampleDev sd = prm.samples[gr.sample];
+    const int N = sd.N, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    V *Ag = reinterpret_cast<V *>(prm.a);
+    // sum |a|^4 per chain in FP64 (one warp per chain, round robin), then the rescaled amplitudes
+    for (int cc = warp; cc < gr.count; cc += 8) {
+        V *a = Ag + sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N;
+        double s4 = 0.0;
+        for (int x = lane; x < N; x += 32) {
+            const V v = a[x];
+            const double u = (double)v.x * v.x + (double)v.y * v.y;
+            s4 += u * u;
+        }
+        for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+        if (lane == 0 && (!(s4 > 0.0) || !isfinite(s4))) record_error(prm.ctl, kErrNaN, 10);
+        const double f = sqrt(sqrt((double)N / s4));
+        for (int x = lane; x < N; x += 32) {
+            V v = a[x];
+            v.x = (real)((double)v.x * f); v.y = (real)((double)v.y * f);
+            a[x] = v;
+        }
+    }
+}
+
+template <typename real, int G>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2) energy_kernel(EnergyParams prm) {
     using V = typename vec2<real>::type;
     constexpr int RS = RowStride<real, G>::value, NCW = 8, WPW = 32 / G, NW = NCW * WPW;
     extern __shared__ __align__(128) unsigned char smem[];
-    const GroupDev gr = prm.groups[blockIdx.x];
+    const int part = (int)(blockIdx.x % (unsigned)prm.parts);
+    const GroupDev gr = prm.groups[blockIdx.x / (unsigned)prm.parts];
     const SampleDev sd = prm.samples[gr.sample];
     const int N = sd.N, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int c = lane % G, worker = warp * WPW + lane / G;
     V *as = reinterpret_cast<V *>(smem);
     double *dred = reinterpret_cast<double *>(smem + (size_t)(N + 2 * APAD) * RS * sizeof(V));
-    __shared__ double s_f[32];
     V *Ag = reinterpret_cast<V *>(prm.a);
     for (int i = tid; i < (N + 2 * APAD) * G; i += blockDim.x) {
         const int x = i / G - APAD, cc = i % G;
@@ -1134,32 +1166,6 @@ __global__ void energy_kernel(EnergyParams prm) {
         as[(x + APAD) * RS + cc] = v;
     }
     __syncthreads();
-    if (prm.renorm) {
-        // sum |a|^4 per chain in FP64 (one warp per chain, round robin)
-        for (int cc = warp; cc < gr.count; cc += NCW) {
-            double s4 = 0.0;
-            for (int x = lane; x < N; x += 32) {
-                const V v = as[(x + APAD) * RS + cc];
-                const double u = (double)v.x * v.x + (double)v.y * v.y;
-                s4 += u * u;
-            }
-            for (int o = 16; o; o >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, o);
-            if (lane == 0) {
-                if (!(s4 > 0.0) || !isfinite(s4)) record_error(prm.ctl, kErrNaN, 10);
-                s_f[cc] = sqrt(sqrt((double)N / s4));
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < N * gr.count; i += blockDim.x) {
-            const int cc = i / N, x = i % N;
-            V v = as[(x + APAD) * RS + cc];
-            const double f = s_f[cc];
-            v.x = (real)((double)v.x * f); v.y = (real)((double)v.y * f);
-            as[(x + APAD) * RS + cc] = v;
-            Ag[sd.a_off + (int64_t)(gr.chain0 - sd.chain0 + cc) * N + x] = v;
-        }
-        __syncthreads();
-    }
     const real *J = reinterpret_cast<const real *>(prm.J);
     const int *bo = prm.bo + sd.tab_off;
     const int *mode_blk = prm.mode_blk + sd.mode_off;
@@ -1167,7 +1173,7 @@ __global__ void energy_kernel(EnergyParams prm) {
     const int total = ebo[N];
     double e = 0.0;
     int x = 0;
-    for (int it = worker; it < total; it += NW) {
+    for (int it = part * NW + worker; it < total; it += NW * prm.parts) {
         while (ebo[x + 1] <= it) ++x;
         const int stlo = x / TS;
         const int sta = (2 * x + 1) / TS;
@@ -1211,11 +1217,21 @@ __global__ void energy_kernel(EnergyParams prm) {
     if (tid < gr.count) {
         double t = 0.0;
         for (int w = 0; w < NCW; ++w) t += dred[w * G + tid];
-        const double E = -prm.cc * t;
-        if (!isfinite(E)) record_error(prm.ctl, kErrNaN, 11);
-        if (prm.E_out) prm.E_out[gr.chain0 + tid] = E;
-        if (prm.E_state) prm.E_state[gr.chain0 + tid] = E;
+        prm.part[((size_t)(blockIdx.x / (unsigned)prm.parts) * prm.parts + part) * 32 + tid] = t;
     }
+}
+
+// E = -cc (sum of the parts, in part order) per chain of a group; one thread per chain.
+__global__ void energy_sum_kernel(EnergyParams prm) {
+    const GroupDev gr = prm.groups[blockIdx.x];
+    const int c = threadIdx.x;
+    if (c >= gr.count) return;
+    double t = 0.0;
+    for (int p = 0; p < prm.parts; ++p) t += prm.part[((size_t)blockIdx.x * prm.parts + p) * 32 + c];
+    const double E = -prm.cc * t;
+    if (!isfinite(E)) record_error(prm.ctl, kErrNaN, 11);
+    if (prm.E_out) prm.E_out[gr.chain0 + c] = E;
+    if (prm.E_state) prm.E_state[gr.chain0 + c] = E;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1312,7 +1328,14 @@ static cudaError_t launch_energy_t(const EnergyParams &p, int ngroups, int maxN,
     const size_t sm = (size_t)(maxN + 2 * APAD) * RowStride<real, G>::value * sizeof(V) + 8 * G * sizeof(double) + 64;
     cudaError_t e = cudaFuncSetAttribute(energy_kernel<real, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    energy_kernel<real, G><<<ngroups, 256, sm, s>>>(p);
+    if (p.parts < 1 || p.parts > kEnergyPartsMax || !p.part) return cudaErrorInvalidValue;
+    if (p.renorm) {
+        renorm_kernel<real, G><<<ngroups, 256, 0, s>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    energy_kernel<real, G><<<ngroups * p.parts, 256, sm, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    energy_sum_kernel<<<ngroups, 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
