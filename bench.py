@@ -878,7 +878,9 @@ def main(argv=None):
                 "cpu_baseline": cpu,
                 "e2e": r["e2e"],
                 "clocks": r["clocks"],
-                "gpu_launches": 5 * args.steps,
+                # per step (one 64-sweep segment): sweep, renormalisation, resync energy, its part sum, measurement,
+                # swap pass, schedule advance
+                "gpu_launches": 7 * args.steps,
                 "fp64_plain_gpu": {"value": r["plain_rate"], "unit": "chain-sweeps/s",
                                    "speedup_fp32": r["value"] / world / r["plain_rate"]},
                 "learned_vs_plain": learned,
