@@ -381,6 +381,10 @@ __device__ __forceinline__ Ranges update_ranges(const SampleDev &sd, const int *
 // 8.62M, the others unchanged; when the field warps still did the gather themselves it paid only from N = 128 on.
 constexpr int kGatherBMinN = 48;
 template <typename real, int G> constexpr bool kGatherB = sizeof(real) == 4;
+// With 8 chains per block the copy warp also draws the random part of every chain's proposal, up to kBD updates
+// ahead, and warp 0 only finishes it at the update's start (measured on GB300: N = 256 bench workload +0.8%;
+// with 16 or 32 chains per block warp 0 drawing the whole proposal itself measured 0.7-1.5% faster).
+template <int G> constexpr bool kCopyDraws = G == 8;
 
 // The coupling J_j[s][{k, s-k}] of quadruplet {j, s-j, k, s-k} (0 where the store holds no such entry):
 // column x* = min(k, s-k) of row s in mode j's run, read from global memory (L2-resident: the run is
@@ -403,49 +407,64 @@ template <typename real> struct Proposal {
     real U;
 };
 
+// The pair move of Sec. III.A.1 in two parts: draw_proposal takes the random numbers of (chain, sweep, update)
+// -- the angles as sqrt(cos theta), sqrt(sin theta), the phases as (cos, sin), and the Metropolis uniform U -- and
+// needs no state, so the copy warp draws it ahead of the update; finish_proposal scales it by
+// K = (|a_j|^4 + |a_k|^4)^(1/4) of the chain's current amplitudes (mode j receives K sqrt(cos theta)).
+template <typename real> struct ProposalDraw {
+    real sqc, sqs, cj, sj, ck, sk, U, pad;
+};
+
 template <typename real>
-__device__ __forceinline__ Proposal<real> make_proposal(uint64_t seed, uint32_t chain_id, uint32_t sweep,
-                                                        uint32_t update, typename vec2<real>::type aj,
-                                                        typename vec2<real>::type ak);
+__device__ __forceinline__ ProposalDraw<real> draw_proposal(uint64_t seed, uint32_t chain_id, uint32_t sweep,
+                                                            uint32_t update);
 
 template <>
-__device__ __forceinline__ Proposal<float> make_proposal<float>(uint64_t seed, uint32_t chain_id, uint32_t sweep,
-                                                                uint32_t update, float2 aj, float2 ak) {
-    Proposal<float> P;
-    P.aj = aj; P.ak = ak;
+__device__ __forceinline__ ProposalDraw<float> draw_proposal<float>(uint64_t seed, uint32_t chain_id, uint32_t sweep,
+                                                                    uint32_t update) {
+    ProposalDraw<float> D;
     const u32x4 w = draw(seed, chain_id, sweep, update, kTagPropose);
-    const float uj = aj.x * aj.x + aj.y * aj.y, uk = ak.x * ak.x + ak.y * ak.y;
-    const float K = sqrtf(sqrtf(uj * uj + uk * uk));
     const float kInv = 2.3283064365386963e-10f;
     const float fj = ((float)w.x + 0.5f) * kInv, fk = ((float)w.y + 0.5f) * kInv, ft = ((float)w.z + 0.5f) * kInv;
-    float sj, cj, sk, ck, st, ct;
-    sincospif(2.0f * fj, &sj, &cj);
-    sincospif(2.0f * fk, &sk, &ck);
+    float st, ct;
+    sincospif(2.0f * fj, &D.sj, &D.cj);
+    sincospif(2.0f * fk, &D.sk, &D.ck);
     sincospif(0.5f * ft, &st, &ct);
-    const float Aj = K * sqrtf(ct), Ak = K * sqrtf(st);
-    P.nj = make_float2(Aj * cj, Aj * sj);
-    P.nk = make_float2(Ak * ck, Ak * sk);
-    P.U = ((float)w.w + 0.5f) * kInv;
-    return P;
+    D.sqc = sqrtf(ct);
+    D.sqs = sqrtf(st);
+    D.U = ((float)w.w + 0.5f) * kInv;
+    D.pad = 0.f;
+    return D;
 }
 
 template <>
-__device__ __forceinline__ Proposal<double> make_proposal<double>(uint64_t seed, uint32_t chain_id,
-                                                                  uint32_t sweep, uint32_t update, double2 aj,
-                                                                  double2 ak) {
-    Proposal<double> P;
-    P.aj = aj; P.ak = ak;
+__device__ __forceinline__ ProposalDraw<double> draw_proposal<double>(uint64_t seed, uint32_t chain_id,
+                                                                      uint32_t sweep, uint32_t update) {
+    ProposalDraw<double> D;
     const u32x4 w = draw(seed, chain_id, sweep, update, kTagPropose);
-    const double uj = aj.x * aj.x + aj.y * aj.y, uk = ak.x * ak.x + ak.y * ak.y;
-    const double K = sqrt(sqrt(uj * uj + uk * uk));
     const double phj = kTwoPi * u01(w.x), phk = kTwoPi * u01(w.y), th = kHalfPi * u01(w.z);
-    const double Aj = K * sqrt(cos(th)), Ak = K * sqrt(sin(th));
-    double sj, cj, sk, ck;
-    sincos(phj, &sj, &cj);
-    sincos(phk, &sk, &ck);
-    P.nj = make_double2(Aj * cj, Aj * sj);
-    P.nk = make_double2(Ak * ck, Ak * sk);
-    P.U = u01(w.w);
+    D.sqc = sqrt(cos(th));
+    D.sqs = sqrt(sin(th));
+    sincos(phj, &D.sj, &D.cj);
+    sincos(phk, &D.sk, &D.ck);
+    D.U = u01(w.w);
+    D.pad = 0.0;
+    return D;
+}
+
+template <typename real>
+__device__ __forceinline__ Proposal<real> finish_proposal(const ProposalDraw<real> &D, typename vec2<real>::type aj,
+                                                          typename vec2<real>::type ak) {
+    Proposal<real> P;
+    P.aj = aj; P.ak = ak;
+    const real uj = aj.x * aj.x + aj.y * aj.y, uk = ak.x * ak.x + ak.y * ak.y;
+    real K;
+    if constexpr (sizeof(real) == 4) K = sqrtf(sqrtf(uj * uj + uk * uk));
+    else K = sqrt(sqrt(uj * uj + uk * uk));
+    const real Aj = K * D.sqc, Ak = K * D.sqs;
+    P.nj.x = Aj * D.cj; P.nj.y = Aj * D.sj;
+    P.nk.x = Ak * D.ck; P.nk.y = Ak * D.sk;
+    P.U = D.U;
     return P;
 }
 
@@ -527,6 +546,7 @@ template <typename real, int G, int NCW> size_t sweep_fixed_bytes(int maxN) {
     if (Sh::PACKED) b += (size_t)(maxN + 2 * APAD) * G * sizeof(float4);      // window table
     if (kGatherB<real, G>) b += (size_t)kBD * maxN * sizeof(real);            // gathered B_jk couplings
     b += (size_t)2 * NCW * G * 8 * sizeof(real);                          // reduction, double-buffered
+    if (kCopyDraws<G>) b += (size_t)kBD * G * sizeof(ProposalDraw<real>);  // proposal draws of kBD updates
     b += (size_t)2 * G * sizeof(Proposal<real>) + 16;                     // proposals, double-buffered
     b += (size_t)G * (sizeof(double) + sizeof(real) + 2 * sizeof(uint32_t) + sizeof(unsigned long long));
     b += (size_t)(2 * 128 + 8) * sizeof(int);                             // bo / xtlo tables
@@ -582,6 +602,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
     real *red = reinterpret_cast<real *>(smem + off);
     off += (size_t)2 * NCW * G * 8 * sizeof(real);
     off = (off + 15) / 16 * 16;
+    ProposalDraw<real> *pdraw = nullptr;  // [kBD][G]
+    if (kCopyDraws<G>) {
+        pdraw = reinterpret_cast<ProposalDraw<real> *>(smem + off);
+        off += (size_t)kBD * G * sizeof(ProposalDraw<real>);
+    }
     Proposal<real> *prop = reinterpret_cast<Proposal<real> *>(smem + off);
     off += (size_t)2 * G * sizeof(Proposal<real>);
     double *cE = reinterpret_cast<double *>(smem + off);
@@ -668,6 +693,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
         const int N = sd.N;
         const int sw0 = ci * spu, sw1 = min(n_sweeps, sw0 + spu);
         const bool gatherB = kGatherB<real, G> && N >= kGatherBMinN;
+        const bool useSlot = kCopyDraws<G> || gatherB;  // the copy warp fills a slot for every update
 
         // ---- unit set-up: tables, chain metadata, amplitudes (consumers); producer starts streaming
         if (!producer) {
@@ -714,6 +740,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
             // ---------------- producer warp: stream J runs of (j,k) for every update of the unit
             const int *bo_g = prm.bo + sd.tab_off;
             const int *xtlo_g = prm.xtlo + sd.tab_off;
+            // identity of chain `lane` of the group (the Philox stream of its proposals): (sample, replica,
+            // temperature index its slot holds)
+            uint32_t pid = 0u;
+            if (lane < gr.count) {
+                const int slot = gr.chain0 + lane;
+                pid = (uint32_t)((gr.sample * prm.R + (slot - sd.chain0) / prm.nT) * prm.nT + prm.label[slot]);
+            }
             bool stop = false;
             for (int sw = sw0; sw < sw1 && !stop; ++sw) {
                 const uint32_t sweep = (uint32_t)(sweep_base + sw);
@@ -723,17 +756,22 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     int j, k;
                     pair_jk(prm.seed, (uint32_t)gr.sample, sweep, (uint32_t)u, N, j, k);
                     const Ranges Rg = update_ranges(sd, bo_g, prm.mode_blk + sd.mode_off, j, k);
-                    if (kGatherB<real, G> && gatherB) {
-                        // the update's B_jk couplings J_j[s][{k, s-k}], s in [max(j,k), min(j,k) + N), gathered
-                        // from L2 by the 32 lanes into a buffer that the field warps read after their blocks
+                    if (useSlot) {
+                        // the update's slot (kBD in a ring, up to kBD updates ahead of the field warps): the random
+                        // part of every chain's proposal (8 chains per block; lane = chain) and, for large N, the B_jk couplings
+                        // J_j[s][{k, s-k}], s in [max(j,k), min(j,k) + N), gathered from L2 by the 32 lanes
                         const int slot = (int)(bcnt % kBD);
                         const uint32_t bph = (bcnt / kBD) & 1u;
                         ++bcnt;
                         if (mbar_wait_bounded(&bempty[slot], bph ^ 1u, prm.ctl, 4, abort_flag)) {
-                            const int sB0 = max(j, k), nB = min(j, k) + N - sB0;
-                            real *bv = bvals + (size_t)slot * prm.maxN;
-                            for (int i = lane; i < nB; i += 32)
-                                bv[i] = b_coupling<real>(J, bo_g, xtlo_g, Rg, sB0 + i, k);
+                            if (kCopyDraws<G> && lane < gr.count)
+                                pdraw[slot * G + lane] = draw_proposal<real>(prm.seed, pid, sweep, (uint32_t)u);
+                            if (kGatherB<real, G> && gatherB) {
+                                const int sB0 = max(j, k), nB = min(j, k) + N - sB0;
+                                real *bv = bvals + (size_t)slot * prm.maxN;
+                                for (int i = lane; i < nB; i += 32)
+                                    bv[i] = b_coupling<real>(J, bo_g, xtlo_g, Rg, sB0 + i, k);
+                            }
                         }
                         mbar_arrive(&bfull[slot]);
                     }
@@ -779,11 +817,28 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     const int jk = s_pair[u];
                     const int j = jk & 0xffff, k = jk >> 16;
                     const Ranges Rg = update_ranges(sd, s_bo, mode_blk, j, k);
-                    // proposal for chain c, drawn by warp 0 into the double-buffered table
+                    // the update's slot from the copy warp (proposal draws with 8 chains per block, B couplings for
+                    // large N); warp 0 puts chain c's proposal into the double-buffered table: finished from the
+                    // copy warp's draw, or drawn whole
+                    int pslot = 0;
+                    uint32_t pph = 0u;
+                    if (useSlot) {
+                        pslot = (int)(bcnt % kBD);
+                        pph = (bcnt / kBD) & 1u;
+                        ++bcnt;
+                    }
                     Proposal<real> *Pp = prop + red_par * G;
-                    if (warp == 0 && wq == 0) {
-                        const V aj = as[(j + APAD) * RS + c], ak = as[(k + APAD) * RS + c];
-                        Pp[c] = make_proposal<real>(prm.seed, cId[c], sweep, (uint32_t)u, aj, ak);
+                    if (warp == 0) {
+                        if constexpr (kCopyDraws<G>) {
+                            const bool dok = mbar_wait_bounded(&bfull[pslot], pph, prm.ctl, 5, abort_flag);
+                            if (dok && wq == 0) {
+                                const V aj = as[(j + APAD) * RS + c], ak = as[(k + APAD) * RS + c];
+                                Pp[c] = finish_proposal<real>(pdraw[pslot * G + c], aj, ak);
+                            }
+                        } else if (wq == 0) {
+                            const V aj = as[(j + APAD) * RS + c], ak = as[(k + APAD) * RS + c];
+                            Pp[c] = finish_proposal<real>(draw_proposal<real>(prm.seed, cId[c], sweep, (uint32_t)u), aj, ak);
+                        }
                     }
                     Partials<real> pr;
                     pr.zero();
@@ -827,17 +882,17 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) sweep_kernel(SweepParams pr
                     // couplings come from the buffer the copy warp filled; worker w takes s = max(j,k) + w + m NW;
                     // for smaller N process_block picks them out of the blocks)
                     if (kGatherB<real, G> && gatherB) {
-                        const int slot = (int)(bcnt % kBD);
-                        const uint32_t bph = (bcnt / kBD) & 1u;
-                        ++bcnt;
-                        if (mbar_wait_bounded(&bfull[slot], bph, prm.ctl, 5, abort_flag)) {
-                            const real *bv = bvals + (size_t)slot * prm.maxN;
+                        if (mbar_wait_bounded(&bfull[pslot], pph, prm.ctl, 5, abort_flag)) {
+                            const real *bv = bvals + (size_t)pslot * prm.maxN;
                             const int sB0 = max(j, k), sB1 = min(j, k) + N;
                             for (int sb = sB0 + worker; sb < sB1; sb += NW)
                                 caxpy(pr.B, bv[sb - sB0], cmulc(as[(sb - j + APAD) * RS + c], as[(sb - k + APAD) * RS + c]));
                         }
+                    }
+                    // every warp is done with the slot (warp 0 copied the proposals out at the update's start)
+                    if (useSlot) {
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&bempty[slot]);
+                        if (lane == 0) mbar_arrive(&bempty[pslot]);
                     }
                     // reduce over the workers of this warp, then across warps through shared memory
                     real v[8] = {pr.hj.x, pr.hj.y, pr.hk.x, pr.hk.y, pr.B.x, pr.B.y, pr.A.x, pr.A.y};
