@@ -76,17 +76,27 @@ def survey_flops_per_chain_sweep(N: int) -> float:
     return 16.0 * 4.0 * count_quads(N)
 
 
-def profiled_traffic():
-    """DRAM bytes per bench sweep launch from the committed ncu summary, or None if the kernel source changed
-    since the counters were taken."""
+def kernel_code_sha(path):
+    """sha1 (12 hex digits) of a CUDA source with its comments and white space removed: the key under which a
+    profile's counters stay valid (a comment edit leaves the compiled kernels unchanged)."""
     import hashlib
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha1(src.encode()).hexdigest()[:12]
+
+
+def profiled_traffic():
+    """DRAM bytes per bench sweep launch from the committed ncu summary, or None if the kernel code changed
+    since the counters were taken."""
     try:
         txt = open(os.path.join(ROOT, "profiles", "sweep_kernel_n256.md")).read()
-        src = open(os.path.join(ROOT, "paper_2511_13508_gb300", "csrc", "pt_sweep.cu"), "rb").read()
+        sha = kernel_code_sha(os.path.join(ROOT, "paper_2511_13508_gb300", "csrc", "pt_sweep.cu"))
     except OSError:
         return None
-    sha = hashlib.sha1(src).hexdigest()[:12]
-    if ("sha1 prefix `%s`" % sha) not in txt:
+    if ("code sha1 prefix `%s`" % sha) not in txt:
         return None
     for line in txt.splitlines():
         if line.startswith("traffic_bytes_per_bench_launch:"):

@@ -514,14 +514,16 @@ __device__ __forceinline__ bool metropolis_accept(double dH, double beta, double
 // ------------------------------------------------------------------------------------------------
 // The persistent sweep kernel.  NCW consumer warps + 1 producer warp.  A consumer lane is
 // (chain c = lane % G, worker q = lane / G); worker w = warp * (32/G) + q takes block w of every
-// chunk of CB = NCW*32/G blocks.  The producer warp streams the J runs of j and k, chunk by chunk,
-// into a ring of NST stages.  Work units = (group, run of sweeps) come from a ticket counter; a unit
+// chunk of CB = NCW*32/G blocks.  The producer (copy) warp streams the J runs of j and k, chunk by chunk,
+// into a ring of NST stages, and fills one slot per update of a second ring (kBD slots): the update's B_jk
+// couplings (FP32, N >= 48) and the random part of every chain's proposal (8 chains per block).  Work units = (group, run of sweeps) come from a ticket counter; a unit
 // waits (bounded) until the previous run of its group has been written back.
 // Ring depth: as many stages as fit next to the amplitude and window tables of the largest N (up to kNstMax), so
 // that the copies of a chunk are issued several chunks ahead of its use (L2 misses of the coupling runs).
 constexpr int kNstMax = 6, kNstMin = 2;
-// Buffers of gathered B_jk couplings (large N, 8 chains per block): the copy warp fills the buffer of an update
-// while it streams the update's coupling runs, up to kBD updates ahead of the field warps.
+// Per-update slots (B_jk couplings for N >= 48 on the FP32 path, proposal draws with 8 chains per block): the copy
+// warp fills an update's slot before it streams the update's coupling runs, up to kBD updates ahead of the field
+// warps.
 constexpr int kBD = 4;
 
 template <typename real, int G, int NCW> struct SweepShape {
