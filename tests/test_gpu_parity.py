@@ -86,6 +86,43 @@ def test_energy_matches_oracle(prec, Ns):
         assert abs(E[c] - ref) <= tol * scale, (c, E[c], ref)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-7)])
+def test_resync_energy_is_exact_and_split_independent(prec, tol):
+    """The resync spreads a group's blocks over several thread blocks (how many depends on the group count)
+    and adds their partial sums in a fixed order: a repeated resync returns bit-identical energies, contexts
+    whose groups (and so splits) differ agree to rounding, and both agree with the oracle's H of the same
+    state (N = 256, the bench's size; an item dropped or counted twice by the split would be off by O(1))."""
+    Ns, R, nT = [256, 256, 256], 2, 8
+    temps = workload.geometric_ladder(0.3, 1.6, nT)
+    Js = couplings(Ns, 2100)
+    rng = np.random.default_rng(77)
+    a = rand_states(Ns, R, nT, rng)
+    shapes = (8, 16)  # (32 chains per block do not fit next to an N = 256 table)
+    Es = []
+    for cpb in shapes:
+        pt = pkg.PT(Ns, Js, temps, R, 5, precision=prec, chains_per_block=cpb, swap_every=0, measure_every=0,
+                    resync_every=0)
+        pt.set_state(a)
+        E1 = pt.energy()
+        E2 = pt.energy()
+        assert np.array_equal(E1, E2)
+        Es.append(E1)
+        pt.close()
+    ref_scale = np.abs(Es[0]).max() + 1.0
+    for E in Es[1:]:
+        assert np.abs(E - Es[0]).max() <= tol * ref_scale
+    quads = oracle.enumerate_quads(256)
+    for c, x in enumerate(split(a, Ns, R, nT)):
+        if c % 7:
+            continue
+        s = c // (R * nT)
+        if prec == "fp32":
+            x = x.astype(np.complex64).astype(np.complex128)
+        ref = oracle.energy(256, quads, Js[s], x)
+        scale = np.sqrt((Js[s] ** 2).sum()) * 4 + abs(ref)
+        assert abs(Es[0][c] - ref) <= (TOL_F32 if prec == "fp32" else TOL_F64) * scale, (c, Es[0][c], ref)
+
+
 # ------------------------------------------------------------------------------------------- local fields
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("N", [4, 10, 16, 34, 64, 128])
