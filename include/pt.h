@@ -218,6 +218,17 @@ int pt_load(pt_ctx *ctx, const void *buf, size_t len);
  * receives {chains_per_block, consumer_warps, sweeps_per_unit}.  PT_EUNSUPPORTED for the plain path. */
 int pt_autotune(pt_ctx *ctx, int trial_sweeps, int *chosen);
 
+/* The sweep-block shape pt_create picks when pt_config.chains_per_block and consumer_warps are 0, for a batch of
+ * n_samples samples whose largest mode count is max_n (even, 4..512), chains_per_sample = replicas x
+ * temperatures, on a device with sm_count multiprocessors (0: unknown).  Host-only, no device call: writes
+ * *chains_per_block (8, 16 or 32) and *consumer_warps.  The rule (measured on GB300): 8 chains from N = 160 on;
+ * for 48 <= N < 160 the most chains per block (32 below N = 96, else 16, then 8) that still give at least 0.8 x
+ * sm_count groups; 16 chains below N = 48; 8 when a sample has at most 8 chains; 11 field warps from N = 48 on,
+ * else 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3.  precision: PT_PREC_FP32 or PT_PREC_FP64 (PT_EINVAL
+ * otherwise, and for out-of-range arguments or NULL outputs). */
+int pt_default_shape(int precision, int max_n, int n_samples, int chains_per_sample, int sm_count,
+                     int *chains_per_block, int *consumer_warps);
+
 /* ---- Learned global-move proposal (built for this engine; the paper has none).  A per-sample masked,
  * block-autoregressive MLP (two hidden layers of 256, BF16 weights on the tensor cores, FP32 accumulate
  * and FP32 master weights with Adam) gives a normalised density q over gauge-fixed coordinates: global

@@ -52,7 +52,7 @@ EXPORTS = ["pt_config_default", "pt_enumerate_quads", "pt_create", "pt_sweep", "
            "pt_last_error", "pt_learn_init", "pt_collect", "pt_train", "pt_global_move", "pt_set_global_every",
            "pt_learn_params", "pt_learn_shape", "pt_learn_eval", "pt_set_global_blocks", "pt_set_global_sampler", "pt_gemm_bf16",
            "pt_energy_fp64_static", "pt_fma_probe", "pt_fmc_graph", "pt_create_graph", "pt_check_wait",
-           "pt_graph_records"]
+           "pt_graph_records", "pt_default_shape"]
 
 _lib = None
 
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.pt_load.argtypes = [vp, vp, ctypes.c_size_t]
         L.pt_counters.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.pt_autotune.argtypes = [vp, i, vp]
+        L.pt_default_shape.argtypes = [i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.pt_learn_init.argtypes = [vp, i, i, i, u64]
         L.pt_collect.argtypes = [vp, i64, i]
         L.pt_train.argtypes = [vp, i, d, vp]
@@ -130,6 +131,16 @@ def fmc_graph(omega, gamma=None) -> np.ndarray:
 def fma_probe(packed, blocks, threads, iters, sink_ptr, stream_ptr):
     """Launches the FP32 FMA-pipe probe (pt_fma_probe): blocks * threads * iters * 32 flops on the stream."""
     _check(None, lib().pt_fma_probe(int(packed), int(blocks), int(threads), int(iters), sink_ptr, stream_ptr))
+
+
+def default_shape(precision, max_n, n_samples, chains_per_sample, sm_count):
+    """Sweep-block shape pt_create picks by default (pt_default_shape, host only):
+    (chains_per_block, consumer_warps)."""
+    G, ncw = ctypes.c_int(), ctypes.c_int()
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(None, lib().pt_default_shape(prec, int(max_n), int(n_samples), int(chains_per_sample), int(sm_count),
+                                        ctypes.byref(G), ctypes.byref(ncw)))
+    return G.value, ncw.value
 
 
 def graph_records(N, quads, J):

@@ -820,6 +820,53 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
                        const double *J, const int64_t *J_offsets, int n_T, const double *temps, int replicas,
                        uint64_t seed, pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream);
 
+// Default shape of the sweep blocks (chains sharing one J stream G, field warps ncw) for the largest N, the sample
+// count and chains per sample, and the device's SM count; G_in > 0 keeps that G.  Measured on GB300
+// (chain-sweeps/s):
+// - N >= 160: 8 chains x 11 warps (N = 192, 32 samples x 64 chains: 1.48M against 1.41M with 16 x 11; N = 256,
+//   16 x 96 chains: 0.694M against 0.481M);
+// - 48 <= N < 160: the most chains per block that still give about one group per SM, from 32, 16, 8 below
+//   N = 96 and from 16, 8 above (N = 64, 64 samples x 64 chains: 32 x 11 24.2M against 20.8M with 16 x 11
+//   and 12.5M with 8 x 11; 16 samples x 64 chains: 8 x 11 10.0M against 5.7M with 32 x 11, which leaves most
+//   SMs idle; N = 128, 64 samples x 64 chains: 16 x 11 4.71M against 4.50M with 32 x 11 and 3.81M with
+//   8 x 11; the ragged batch N in {32..128}: 16 x 11 8.91M against 8.38M with 8 x 11), 32 x 11 (16 x 11 from
+//   N = 96) when none does;
+// - N < 48: 16 x 7;
+// - at most 8 chains per sample: 8 chains per block.
+// Field warps: 11 from N = 48 on (N = 64, 64 samples: 32 x 11 22.3M chain-sweeps/s against 21.6M with 32 x 7;
+// ragged batch: 16 x 11 8.24M against 7.53M with 16 x 7), else 7.  FP64: 8 x 7 from N = 128 on, else 16 x 3
+// (N = 64, 64 samples: 16 x 3 685k, 8 x 7 521k).
+static void default_shape(bool dbl, int maxN, int S, int chains_ps, int sms, int G_in, int *G_out, int *ncw_out) {
+    int G = G_in;
+    if (G == 0) {
+        if (dbl) G = (maxN >= 128) ? 8 : 16;
+        else if (maxN >= 160) G = 8;
+        else if (maxN >= 48) {
+            const int gmax = maxN >= 96 ? 16 : 32;
+            for (int g : {32, 16, 8}) {
+                if (G == 0 && g <= gmax && sms > 0 && (int64_t)S * ((chains_ps + g - 1) / g) >= (int64_t)sms * 4 / 5) G = g;
+            }
+            if (G == 0) G = (gmax == 32 && chains_ps >= 32) ? 32 : 16;
+        } else {
+            G = 16;
+        }
+        if (G > 8 && chains_ps <= 8) G = 8;
+    }
+    *G_out = G;
+    if (dbl) *ncw_out = (G == 16) ? 3 : 7;
+    else *ncw_out = (maxN >= 48) ? 11 : 7;
+}
+
+int pt_default_shape(int precision, int max_n, int n_samples, int chains_per_sample, int sm_count,
+                     int *chains_per_block, int *consumer_warps) {
+    if ((precision != PT_PREC_FP32 && precision != PT_PREC_FP64) || max_n < 4 || max_n > 512 || (max_n & 1) ||
+        n_samples < 1 || chains_per_sample < 1 || sm_count < 0 || !chains_per_block || !consumer_warps)
+        return fail(nullptr, PT_EINVAL, "pt_default_shape: bad argument");
+    default_shape(precision == PT_PREC_FP64, max_n, n_samples, chains_per_sample, sm_count, 0, chains_per_block,
+                  consumer_warps);
+    return PT_OK;
+}
+
 int pt_create(pt_ctx **out, const pt_config *cfg_in, int S, const int32_t *Nv, const double *J,
               const int64_t *J_offsets, int n_T, const double *temps, int replicas, uint64_t seed,
               pt_alloc_fn alloc, pt_free_fn free_, void *alloc_user, void *stream) {
@@ -936,40 +983,15 @@ static int create_impl(pt_ctx **out, const pt_config *cfg_in, int S, const int32
 
     // ---- scheduling shape
     const int chains_ps = replicas * n_T;
-    // shape of the sweep blocks (chains sharing one J stream, field warps); measured on GB300 (chain-sweeps/s):
-    // - N >= 160: 8 chains x 11 warps (N = 192, 32 samples x 64 chains: 1.48M against 1.41M with 16 x 11; N = 256,
-    //   16 x 96 chains: 0.694M against 0.481M);
-    // - 48 <= N < 160: the most chains per block that still give about one group per SM, from 32, 16, 8 below
-    //   N = 96 and from 16, 8 above (N = 64, 64 samples x 64 chains: 32 x 11 24.2M against 20.8M with 16 x 11
-    //   and 12.5M with 8 x 11; 16 samples x 64 chains: 8 x 11 10.0M against 5.7M with 32 x 11, which leaves most
-    //   SMs idle; N = 128, 64 samples x 64 chains: 16 x 11 4.71M against 4.50M with 32 x 11 and 3.81M with
-    //   8 x 11; the ragged batch N in {32..128}: 16 x 11 8.91M against 8.38M with 8 x 11), 32 x 11 (16 x 11 from
-    //   N = 96) when none does;
-    // - N < 48: 16 x 7.
-    // FP64: 8 x 7 from N = 128 on, else 16 x 3
     int G = cfg.chains_per_block, ncw = 0;
     if (c->gfp32) G = 8;  // the group kernels hold 8 chains per block
-    if (G == 0) {
-        if (c->dbl) G = (c->maxN >= 128) ? 8 : 16;  // FP64, N = 64, 64 samples: 16 x 3 685k, 8 x 7 521k
-        else if (c->maxN >= 160) G = 8;
-        else if (c->maxN >= 48) {
-            int dev = 0, sms = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                sms = 0;
-            const int gmax = c->maxN >= 96 ? 16 : 32;
-            for (int g : {32, 16, 8}) {
-                if (G == 0 && g <= gmax && sms > 0 && (int64_t)S * ((chains_ps + g - 1) / g) >= (int64_t)sms * 4 / 5) G = g;
-            }
-            if (G == 0) G = (gmax == 32 && chains_ps >= 32) ? 32 : 16;
-        } else {
-            G = 16;
-        }
-        if (G > 8 && chains_ps <= 8) G = 8;
+    {
+        int dev = 0, sms = 0;
+        if (G == 0 && (cudaGetDevice(&dev) != cudaSuccess ||
+                       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+            sms = 0;
+        default_shape(c->dbl, c->maxN, S, chains_ps, sms, G, &G, &ncw);
     }
-    // FP32 field warps: 11 from N = 48 on (N = 64, 64 samples: 32 x 11 22.3M chain-sweeps/s against 21.6M with
-    // 32 x 7; ragged batch: 16 x 11 8.24M against 7.53M with 16 x 7), else 7
-    if (c->dbl) ncw = (G == 16) ? 3 : 7;
-    else ncw = (c->maxN >= 48) ? 11 : 7;
     if (cfg.consumer_warps > 0) ncw = cfg.consumer_warps;
     if (!c->plain && !c->gfp32 && !sweep_variant_exists(c->dbl, G, ncw)) return bail(fail(c, PT_EINVAL, "pt_create: unsupported chains_per_block"));
     c->G = G; c->ncw = ncw;

@@ -73,3 +73,31 @@ def test_create_rejects_bad_arguments_before_device_work(L):
     rc, h, msg = _create(L, [16], Jn, off, [1.0])
     assert rc == -5 and "non-finite" in msg
     assert L.pt_destroy(None) == 0
+
+
+@pytest.mark.parametrize("prec,max_n,S,chains,sms,expect", [
+    ("fp32", 256, 16, 96, 152, (8, 11)),    # the bench workload: 8 chains from N = 160 on
+    ("fp32", 192, 32, 64, 152, (8, 11)),
+    ("fp32", 128, 96, 48, 152, (16, 11)),   # the ragged batch (largest N 128): at most 16 chains from N = 96
+    ("fp32", 96, 64, 64, 152, (16, 11)),
+    ("fp32", 96, 2, 16, 152, (16, 11)),     # too few groups for any size: 16 chains from N = 96
+    ("fp32", 64, 64, 64, 152, (32, 11)),    # the batched N = 64 workload: 128 groups of 32 >= 0.8 x 152
+    ("fp32", 64, 16, 64, 152, (8, 11)),     # 16 samples: only groups of 8 give enough of them
+    ("fp32", 64, 2, 64, 152, (32, 11)),     # none does: 32 chains
+    ("fp32", 64, 64, 64, 0, (32, 11)),      # SM count unknown
+    ("fp32", 48, 64, 64, 152, (32, 11)),
+    ("fp32", 32, 8, 16, 152, (16, 7)),      # below N = 48: 16 x 7
+    ("fp32", 16, 4, 8, 152, (8, 7)),        # at most 8 chains per sample: 8 per block
+    ("fp64", 64, 64, 64, 152, (16, 3)),
+    ("fp64", 128, 8, 16, 152, (8, 7)),
+])
+def test_default_shape_rule(L, prec, max_n, S, chains, sms, expect):
+    assert pkg.default_shape(prec, max_n, S, chains, sms) == expect
+
+
+def test_default_shape_rejects_bad_arguments(L):
+    G, ncw = ctypes.c_int(), ctypes.c_int()
+    for args in [(2, 64, 1, 1, 152), (0, 65, 1, 1, 152), (0, 2, 1, 1, 152), (0, 514, 1, 1, 152), (0, 64, 0, 1, 152),
+                 (0, 64, 1, 0, 152), (0, 64, 1, 1, -1)]:
+        assert L.pt_default_shape(*args, ctypes.byref(G), ctypes.byref(ncw)) == -1, args
+    assert L.pt_default_shape(0, 64, 1, 1, 152, None, ctypes.byref(ncw)) == -1
