@@ -353,7 +353,7 @@ int pt_energy_fp64_static(int N, int n_chains, const double *J, const double *a,
  * conj(a_q3), Sec. II.C with Eq. (4)):
  *   offsets [N+1]    records of mode l are rec[offsets[l] .. offsets[l+1]), one per quadruplet holding l, in
  *                    list order;
- *   rec [4 nq][4]    int32 (A, B, C, w): the three other modes as row offsets mode * 9 of the kernels'
+ *   rec [4 nq][4]    int32 (A, B, C, w): the three other modes as row offsets mode * 8 of the kernels'
  *                    amplitude table, ordered so that the record's contribution to the local field of l
  *                    (Sec. III.A.3, H = -cc Re(conj(a_l) h_l) + terms without l) is J a_A a_B conj(a_C);
  *                    w = position of l | positions of A, B, C << 2, 4, 6;

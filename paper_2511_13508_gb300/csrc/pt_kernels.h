@@ -126,9 +126,9 @@ cudaError_t launch_measure(const MeasureParams &p, cudaStream_t s);
 
 // Plain FP64 path: the paper's design restated (one block per chain, one thread per quadruplet term).
 // pt_graph.cu: FP32 sweep / energy on explicit interaction lists (one block per group of 8 chains)
-// Row stride (in float2) of the FP32 group kernels' amplitude table: 8 chains + 1 pad.  The incidence records
+// Row stride (in float2) of the FP32 group kernels' amplitude table: the 8 chains, unpadded.  The incidence records
 // hold partner modes as row offsets (mode x this).
-constexpr int kGraphRowStride = 9;
+constexpr int kGraphRowStride = 8;
 
 struct GraphParams {
     const SampleDev *samples;

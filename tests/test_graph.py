@@ -138,8 +138,8 @@ def test_incidence_records_decode_to_the_oracle_fields(kind):
         tot = 0j
         for e, q in zip(range(off[l], off[l + 1]), held):
             A, B, C, w = (int(v) for v in rec[e])
-            assert A % 9 == 0 and B % 9 == 0 and C % 9 == 0
-            mA, mB, mC = A // 9, B // 9, C // 9
+            assert A % 8 == 0 and B % 8 == 0 and C % 8 == 0
+            mA, mB, mC = A // 8, B // 8, C // 8
             pos, pA, pB, pC = w & 3, (w >> 2) & 3, (w >> 4) & 3, (w >> 6) & 3
             assert sorted([pos, pA, pB, pC]) == [0, 1, 2, 3]
             assert quads[q][pos] == l and quads[q][pA] == mA and quads[q][pB] == mB and quads[q][pC] == mC
